@@ -1,0 +1,81 @@
+"""Pins for the oracle's FP step (Eq. (7)) and cycling driver (Algorithm 3) on small
+synthetic problems.
+
+The strongest check is exact: the FP recursion Eq. (6) says
+grad l(x_{k+1}) + alpha (x_{k+1} - f(x_k)) = 0, so the gradient of the objective (Eq. (5))
+at x_{k+1} equals alpha (f(x_k) - f(x_{k+1})). The gradient is formed from H and H^T
+directly, so a dropped sigma^2, alpha or conjugate in the solve fails this test."""
+import numpy as np
+import pytest
+
+from oracle import fp, red
+from oracle import operators as ops
+from oracle.nlm import nlm
+from paper_1805_02158_gb300 import synth
+
+
+def small_deblur(seed=0, side=24):
+    return synth.make_deblur(seed, side, side, synth.uniform_psf(5), np.sqrt(2.0))
+
+
+def small_sr(seed=0, side=24):
+    return synth.make_sr(seed, side, side, synth.gaussian_psf(7, 1.6), 3, 5.0)
+
+
+@pytest.mark.parametrize("make", [small_deblur, small_sr])
+def test_fp_step_satisfies_first_order_recursion(make):
+    p = make()
+    F = fp.FPOperator(p.y, p.psf, p.y.shape if p.scale == 1 else (p.height, p.width), p.scale,
+                      p.sigma, p.alpha, cg_iters=400)
+    x = p.x0
+    x1, fx = F.step_with_f(x)
+    fx1 = nlm(x1)
+    g = red.gradient(x1, fx1, p.y, F.otf, p.scale, p.sigma, p.alpha)
+    expect = p.alpha * (fx - fx1)
+    np.testing.assert_allclose(g, expect, rtol=1e-6, atol=1e-7 * np.abs(expect).max())
+
+
+def test_fp_converges_and_gradient_vanishes():
+    p = small_deblur(1)
+    F = fp.FPOperator(p.y, p.psf, p.y.shape, 1, p.sigma, p.alpha)
+    rcs = []
+    x, st = red.solve(F, p.x0, "none", max_calls=120,
+                      callback=lambda c, v: rcs.append(v.copy()))
+    changes = [red.rel_change(rcs[i + 1], rcs[i]) for i in range(len(rcs) - 1)]
+    # slow linear convergence (the reason for extrapolation), but steadily contracting
+    assert changes[-1] < 0.03 * changes[0]
+    assert changes[-1] < changes[len(changes) // 2]
+    g = red.gradient(x, nlm(x), p.y, F.otf, 1, p.sigma, p.alpha)
+    g0 = red.gradient(p.x0, nlm(p.x0), p.y, F.otf, 1, p.sigma, p.alpha)
+    assert np.linalg.norm(g) < 1e-3 * np.linalg.norm(g0)
+
+
+def test_driver_counts_and_termination():
+    p = small_deblur(2, 16)
+    F = fp.FPOperator(p.y, p.psf, p.y.shape, 1, p.sigma, p.alpha)
+    calls = []
+    x, st = red.solve(F, p.x0, "rre", m=0, kappa=4, max_calls=23, callback=lambda c, v: calls.append(c))
+    assert st["fp_calls"] == 23 and calls == list(range(1, 24))
+    assert st["ve_steps"] == 4  # after calls 5, 10, 15, 20
+    x, st = red.solve(F, p.x0, "none", max_calls=500, tol=1e-3)
+    assert st["fp_calls"] < 500 and st["rel_change"] < 1e-3
+    # the FP iterate returned is F applied to the previous one
+    x2, st2 = red.solve(F, p.x0, "none", max_calls=st["fp_calls"] - 1)
+    np.testing.assert_allclose(F(x2), x, atol=1e-10)
+
+
+def test_ve_reaches_fp_objective_in_fewer_calls():
+    """Sec. IV: FP-MPE/RRE attains E(x*_FP) in fewer denoiser calls than FP."""
+    p = small_deblur(3, 32)
+    F = fp.FPOperator(p.y, p.psf, p.y.shape, 1, p.sigma, p.alpha)
+    budget = 80
+    xfp, _ = red.solve(F, p.x0, "none", max_calls=budget)
+    e_fp = red.objective(xfp, nlm(xfp), p.y, F.otf, 1, p.sigma, p.alpha)
+    for method in ("mpe", "rre"):
+        reached = []
+
+        def cb(c, v):
+            if not reached and red.objective(v, nlm(v), p.y, F.otf, 1, p.sigma, p.alpha) <= e_fp:
+                reached.append(c)
+        red.solve(F, p.x0, method, m=0, kappa=4, max_calls=budget, callback=cb)
+        assert reached and reached[0] < 0.75 * budget, (method, reached)
