@@ -1,0 +1,355 @@
+"""Benchmark: batched RED deblurring solves with RRE extrapolation on one GB300.
+
+Workload (the paper's deblurring scale, Sec. IV-A, with synthetic images): 10 seeded
+256x256 piecewise-smooth images per GPU, 25x25 Gaussian PSF (std 1.6) with circular
+boundary, noise sigma sqrt(2), NLM 5x5 / 11x11 / h = 10, alpha = 0.02, RRE with k = 5
+(Algorithm 3, m = 0), FP32 images, FP64-accurate extrapolation. One step = one batched
+solve of all 10 problems for the paper's budget of 200 FP steps (denoiser calls) each.
+
+value = Mpix-iter/s = images x pixels x FP steps / device time (inputs resident in HBM;
+L2 flushed between timed steps). e2e = the same metric through red_batch_solve_host with
+pinned host buffers (copies inside the timed region). --impl reference times the FP64
+oracle on the host cores on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): replicas, each rank solves its own 10 problems (weak scaling).
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RED solves/s and Mpix-iter/s at <=0.01 dB vs FP64 oracle, VE vs plain FP; p50/p99 ms"
+UNIT = "Mpix-iter/s"
+N_IMAGES = 10
+SIDE = 256
+CALLS = 200
+VE_K = 5
+NLM_OPS_PER_PIXEL_OFFSET = 8       # FP32-pipe ops of the separable NLM per pixel and offset
+NLM_OFFSETS = 121
+WORKLOAD = ("deblur 256x256 x10 images per GPU, Gaussian 25x25 std 1.6, noise sqrt2, "
+            "NLM 5x5/11x11 h=10, alpha 0.02, RRE k=5 m=0, 200 FP steps per solve")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problems(rank):
+    from paper_1805_02158_gb300 import synth
+    return [synth.deblur_gauss256(rank * N_IMAGES + i, SIDE) for i in range(N_IMAGES)]
+
+
+def cpu_oracle_sample(seconds_target=12.0):
+    """The FP64 oracle as it stands: Algorithm 3 (RRE, kappa = 4) on one 256x256 problem
+    of the workload for as many FP steps as fit in the target (>= 2)."""
+    from oracle import fp as ofp
+    from oracle import red as ored
+    from paper_1805_02158_gb300 import synth
+    p = synth.deblur_gauss256(0, SIDE)
+    y = p.y.astype(np.float32).astype(np.float64)
+    F = ofp.FPOperator(y, p.psf, (SIDE, SIDE), 1, p.sigma, p.alpha)
+    t0 = time.perf_counter()
+    F(y)
+    one = time.perf_counter() - t0
+    calls = max(2, min(12, int(seconds_target / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    ored.solve(F, y, "rre", m=0, kappa=VE_K - 1, max_calls=calls)
+    dt = time.perf_counter() - t0
+    return {"value": SIDE * SIDE * calls / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 image 256x256, {calls} FP steps of RRE k=5 (Algorithm 3), FP64 NumPy, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(seconds_target=4.0)
+        if i >= args.warmup:
+            steps.append(r)
+    value = float(np.mean([s["value"] for s in steps]))
+    calls_ms = 1e3 * SIDE * SIDE * CALLS * N_IMAGES / (value * 1e6)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": calls_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": steps[-1]["sample"] + " per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ve_vs_fp_study(problems, Ps, torch, red):
+    """Denoiser calls RRE needs to reach plain FP's PSNR and objective after 200 calls
+    (the Table I criterion), per image; outside the timed region."""
+    from paper_1805_02158_gb300.red import Batch
+    n = len(problems)
+    x0s = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
+    outs = [torch.empty_like(x) for x in x0s]
+    fp_cfgs = [red.config_for(p, ve="none") for p in problems]
+    fpP = [red.Problem(c, x) for c, x in zip(fp_cfgs, x0s)]
+    B = Batch(fpP)
+    B.solve(x0s, outs, CALLS, 0.0)
+    xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
+    psnr_fp = [10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2)) for x, p in zip(xfp, problems)]
+    e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
+    Bv = Batch(Ps)
+    need_psnr = [None] * n
+    need_cost = [None] * n
+    for calls in range(5, CALLS + 1, 5):
+        Bv.solve(x0s, outs, calls, 0.0)
+        for i, (o, p, P) in enumerate(zip(outs, problems, Ps)):
+            x = o.cpu().numpy().astype(np.float64)
+            ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
+            if need_psnr[i] is None and ps >= psnr_fp[i]:
+                need_psnr[i] = calls
+            if need_cost[i] is None and P.objective(o) <= e_fp[i]:
+                need_cost[i] = calls
+        if all(v is not None for v in need_psnr + need_cost):
+            break
+    fill = lambda v: [c if c is not None else CALLS for c in v]  # noqa: E731
+    return {"fp_calls": CALLS, "fp200_psnr_db_mean": float(np.mean(psnr_fp)),
+            "rre_calls_to_fp200_psnr": fill(need_psnr), "rre_calls_to_fp200_cost": fill(need_cost),
+            "rre_calls_to_fp200_psnr_mean": float(np.mean(fill(need_psnr))),
+            "rre_calls_to_fp200_cost_mean": float(np.mean(fill(need_cost)))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-study", action="store_true", help="skip the VE-vs-FP call study")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1805_02158_gb300 import red
+
+    problems = make_problems(rank)
+    ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
+    Ps = [red.Problem(red.config_for(p, ve="rre", ve_k=VE_K), y) for p, y in zip(problems, ys)]
+    B = red.Batch(Ps)
+    B.set_phase_timing(True)
+    x0s = [y.clone() for y in ys]
+    outs = [torch.empty_like(y) for y in ys]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        B.solve(x0s, outs, CALLS, 0.0)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    step_ms, nlm_ms, fft_ms, gram_ms, comb_ms = [], [], [], [], []
+    l0 = red.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict the working set from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.cuda.nvtx.range_push("timed_step")
+        B.solve(x0s, outs, CALLS, 0.0)
+        torch.cuda.nvtx.range_pop()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        nlm_ms.append(B.phase_ms(red.PHASE_NLM)[0])
+        fft_ms.append(B.phase_ms(red.PHASE_FFT)[0])
+        gram_ms.append(B.phase_ms(red.PHASE_GRAM)[0])
+        comb_ms.append(B.phase_ms(red.PHASE_COMBINE)[0])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = red.kernel_launches() - l0
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    pix = SIDE * SIDE * N_IMAGES
+    units = pix * CALLS * args.steps * world
+    value = units / (total_ms / 1e3) / 1e6
+    solves_per_s = N_IMAGES * world * args.steps / (total_ms / 1e3)
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    y_h = [torch.from_numpy(p.y.astype(np.float32)).pin_memory() for p in problems]
+    x0_h = [y.clone().pin_memory() for y in y_h]
+    out_h = [torch.empty_like(y).pin_memory() for y in y_h]
+    B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(sum(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = units / (e2e_total / 1e3) / 1e6
+    h2d = sum(int(y.numel()) * 4 for y in y_h) + sum(int(x.numel()) * 4 for x in x0_h)
+    d2h = sum(int(o.numel()) * 4 for o in out_h)
+
+    pk, pk_src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    nlm_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12          # FP32 lane-ops, T/s
+    nlm_avg = float(np.mean(nlm_ms))
+    nlm_ops = pix * NLM_OFFSETS * NLM_OPS_PER_PIXEL_OFFSET
+    nlm_achieved = nlm_ops / (nlm_avg / 1e3) / 1e12
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    fft_bytes = pix * 14                                   # read f, C, G; write x (per FP step)
+    gram_bytes = pix * 4 * (VE_K + 1)
+    comb_bytes = pix * 4 * (VE_K + 1)
+    kern = {
+        "fft_solve": {"ms": float(np.mean(fft_ms)), "algorithmic_bytes": fft_bytes,
+                      "GBps": fft_bytes / (np.mean(fft_ms) / 1e3) / 1e9},
+        "gram": {"ms": float(np.mean(gram_ms)), "algorithmic_bytes": gram_bytes,
+                 "GBps": gram_bytes / (np.mean(gram_ms) / 1e3) / 1e9},
+        "combine": {"ms": float(np.mean(comb_ms)), "algorithmic_bytes": comb_bytes,
+                    "GBps": comb_bytes / (np.mean(comb_ms) / 1e3) / 1e9},
+        "hbm_peak_GBps": hbm,
+    }
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "nlm_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    study = None
+    if not args.no_study and rank == 0:
+        study = ve_vs_fp_study(problems, Ps, torch, red)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+        return
+    cpu = cpu_oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images_per_gpu": N_IMAGES, "side": SIDE,
+                   "fp_calls_per_solve": CALLS, "ve": "rre", "k": VE_K,
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "solves_per_s": solves_per_s,
+        "roofline": {"bound": "alu", "kernel": "k_nlm", "achieved": nlm_achieved,
+                     "peak": nlm_peak, "unit": "Top/s (FP32 lane-ops)",
+                     "frac": nlm_achieved / nlm_peak, "traffic": traffic,
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_src} max clock)",
+                     "launch_ms": nlm_avg},
+        "kernels": kern,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "ve_vs_fp": study,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

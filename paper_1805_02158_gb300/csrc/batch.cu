@@ -1,0 +1,521 @@
+// Batched solves (Algorithm 3 for many problems at once), cycles replayed as CUDA graphs,
+// and the launch-shape autotuner.
+//
+// A batch owns a device table of problem descriptors and per-problem termination states.
+// Every phase of a cycle is one launch over all problems (work lists of tiles, rows,
+// columns, chunks; one cluster per super-resolution problem). Problems that have
+// terminated skip their work inside the kernels, so the host only reads the states back
+// once per cycle (or never, for a fixed FP-call budget) and a cycle is a fixed sequence
+// of launches on fixed ring slots, captured once as a CUDA graph and replayed.
+//
+// Autotuner: the launch shapes (NLM CTA height, rows per row-FFT CTA, columns per
+// column-FFT CTA, CTAs per super-resolution cluster) only change how fixed work units
+// are grouped into CTAs, never a pixel's arithmetic, so every candidate gives bitwise the
+// same result. Candidates are timed with CUDA events on the batch's own buffers; the
+// choice is cached per process and, if RED_TUNE_CACHE names a file, across processes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "red.h"
+#include "runtime.h"
+
+using namespace red;
+
+red_batch_s::~red_batch_s() {
+  for (auto &e : phase_events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (graph) cudaGraphExecDestroy(graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  plan.release();
+  if (d_pds) cudaFree(d_pds);
+  if (d_states) cudaFree(d_states);
+  if (d_ptrs) cudaFree(d_ptrs);
+  if (h_states) cudaFreeHost(h_states);
+  if (h_ptrs) cudaFreeHost(h_ptrs);
+}
+
+namespace red {
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, LaunchCfg> g_tune_mem;
+
+bool tune_lookup(const std::string &key, LaunchCfg &out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_mem.find(key);
+  if (it != g_tune_mem.end()) {
+    out = it->second;
+    return true;
+  }
+  const char *path = std::getenv("RED_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    std::istringstream ss(line);
+    std::string k;
+    LaunchCfg c;
+    if (ss >> k >> c.nlm_wy >> c.fft_rows >> c.fft_cols >> c.sr_cluster && k == key) {
+      g_tune_mem[key] = c;
+      out = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+void tune_store(const std::string &key, const LaunchCfg &c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_mem[key] = c;
+  const char *path = std::getenv("RED_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream out(path, std::ios::app);
+  out << key << " " << c.nlm_wy << " " << c.fft_rows << " " << c.fft_cols << " " << c.sr_cluster
+      << "\n";
+}
+
+std::string tune_key(const red_batch_s *b) {
+  std::vector<std::string> parts;
+  for (auto *p : b->probs) {
+    std::ostringstream o;
+    o << p->cfg.task << "x" << p->cfg.height << "x" << p->cfg.width << "s" << p->cfg.storage;
+    parts.push_back(o.str());
+  }
+  std::sort(parts.begin(), parts.end());
+  std::ostringstream key;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  key << "v1|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
+  std::string k = key.str();
+  std::replace(k.begin(), k.end(), ' ', '_');
+  return k;
+}
+
+void upload_pds(red_batch_s *b) {
+  for (size_t i = 0; i < b->pds.size(); ++i) {
+    b->pds[i].n_row_items = b->plan.n_row_items[i];
+    b->pds[i].st = b->d_states + i;
+  }
+  CUDA_OK(cudaMemcpy(b->d_pds, b->pds.data(), sizeof(ProbDev) * b->pds.size(),
+                     cudaMemcpyHostToDevice));
+  prepare_launch_attrs(b->plan);
+}
+
+float time_ms(cudaStream_t s, int reps, const std::function<void()> &fn) {
+  cudaEvent_t e0, e1;
+  CUDA_OK(cudaEventCreate(&e0));
+  CUDA_OK(cudaEventCreate(&e1));
+  fn();  // warm-up
+  CUDA_OK(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) fn();
+  CUDA_OK(cudaEventRecord(e1, s));
+  CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
+}
+
+// Coordinate-wise search over the launch-shape knobs, each timed on the batch.
+LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
+  LaunchCfg best;
+  const int n = (int)b->probs.size();
+  StepArgs sa{0, 1, nullptr, nullptr, 0};
+  const int reps = 3;
+  auto rebuild = [&](const LaunchCfg &c) {
+    b->plan.build(b->pds, c);
+    upload_pds(b);
+  };
+  // NLM tile height
+  {
+    float bt = 1e30f;
+    LaunchCfg c = best;
+    for (int wy : {1, 2, 4, 8}) {
+      c.nlm_wy = wy;
+      rebuild(c);
+      const float t = time_ms(s, reps, [&] {
+        CUDA_OK(launch_nlm(b->d_pds, b->plan.d_items + b->plan.off_nlm, b->plan.n_nlm, wy, sa, 0, s));
+      });
+      if (t < bt) { bt = t; best.nlm_wy = wy; }
+    }
+  }
+  bool has_deblur = false, has_sr = false;
+  for (auto *p : b->probs) (p->cfg.task == RED_DEBLUR ? has_deblur : has_sr) = true;
+  if (has_deblur) {
+    float bt = 1e30f;
+    LaunchCfg c = best;
+    for (int r : {0, 2, 4, 8, 16}) {
+      c.fft_rows = r;
+      rebuild(c);
+      const Plan &pl = b->plan;
+      const float t = time_ms(s, reps, [&] {
+        CUDA_OK(launch_fft_r2c(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
+                               pl.row_buf_cap, nullptr, nullptr, 0, s));
+        CUDA_OK(launch_fft_c2r(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
+                               pl.row_buf_cap, sa, s));
+      });
+      if (t < bt) { bt = t; best.fft_rows = r; }
+    }
+    bt = 1e30f;
+    c = best;
+    for (int q : {0, 2, 4, 8}) {
+      c.fft_cols = q;
+      rebuild(c);
+      const Plan &pl = b->plan;
+      const float t = time_ms(s, reps, [&] {
+        CUDA_OK(launch_fft_cols(b->d_pds, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,
+                                pl.col_buf_cap, 1, nullptr, 0, s));
+      });
+      if (t < bt) { bt = t; best.fft_cols = q; }
+    }
+  }
+  if (has_sr) {
+    float bt = 1e30f;
+    LaunchCfg c = best;
+    for (int cl : {4, 8}) {
+      c.sr_cluster = cl;
+      rebuild(c);
+      const Plan &pl = b->plan;
+      const float t = time_ms(s, 1, [&] {
+        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, cl, sa, s));
+      });
+      if (t < bt) { bt = t; best.sr_cluster = cl; }
+    }
+  }
+  (void)n;
+  return best;
+}
+
+// Phase timing: events are created once per (cycle op, phase) and recorded around the
+// phase's launches, so a graph replay re-records them.
+struct PhaseScope {
+  red_batch_s *b;
+  cudaStream_t s;
+  size_t next = 0;
+  void begin(int phase) {
+    if (!b->phase_timing) return;
+    if (next >= b->phase_events.size()) {
+      red_batch_s::PhaseEv e{phase, nullptr, nullptr};
+      CUDA_OK(cudaEventCreate(&e.a));
+      CUDA_OK(cudaEventCreate(&e.b));
+      b->phase_events.push_back(e);
+    }
+    CUDA_OK(cudaEventRecord(b->phase_events[next].a, s));
+  }
+  void end() {
+    if (!b->phase_timing) return;
+    CUDA_OK(cudaEventRecord(b->phase_events[next].b, s));
+    ++next;
+  }
+};
+
+void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
+  const int n = (int)b->probs.size();
+  const Plan &pl = b->plan;
+  PhaseScope ps{b, s};
+  for (const CycleOp &op : b->ops) {
+    if (op.kind == 0) {
+      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
+      ps.begin(RED_PHASE_NLM);
+      CUDA_OK(launch_nlm(b->d_pds, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, 0, s));
+      ps.end();
+      if (pl.n_rows) {
+        ps.begin(RED_PHASE_FFT);
+        CUDA_OK(launch_fft_r2c(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
+                               pl.row_buf_cap, nullptr, nullptr, 1, s));
+        CUDA_OK(launch_fft_cols(b->d_pds, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,
+                                pl.col_buf_cap, 1, nullptr, 1, s));
+        CUDA_OK(launch_fft_c2r(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
+                               pl.row_buf_cap, sa, s));
+        ps.end();
+      }
+      if (pl.n_sr) {
+        ps.begin(RED_PHASE_CG);
+        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, sa, s));
+        ps.end();
+      }
+    } else {
+      VeArgs va{};
+      for (size_t i = 0; i < op.slots.size(); ++i) va.slots[i] = op.slots[i];
+      va.nvec = (int)op.slots.size();
+      va.out_slot = op.out;
+      va.update_state = 1;
+      ps.begin(RED_PHASE_GRAM);
+      CUDA_OK(launch_gram(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
+      ps.end();
+      ps.begin(RED_PHASE_VESOLVE);
+      CUDA_OK(launch_ve_solve(b->d_pds, n, va.nvec, va.update_state, s));
+      ps.end();
+      ps.begin(RED_PHASE_COMBINE);
+      CUDA_OK(launch_combine(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
+      ps.end();
+    }
+  }
+}
+
+void ensure_ready(red_batch_s *b, cudaStream_t s) {
+  if (!b->ready) {
+    LaunchCfg c;
+    if (!tune_lookup(b->tune_key, c)) {
+      c = autotune(b, s);
+      tune_store(b->tune_key, c);
+    }
+    b->lc = c;
+    b->plan.build(b->pds, c);
+    upload_pds(b);
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    b->ready = true;
+  }
+  const char *ng = std::getenv("RED_NO_GRAPHS");
+  if (!b->graph && !(ng && *ng == '1')) {
+    if (!b->cap_stream) CUDA_OK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    const uint64_t before = red_kernel_launches();
+    CUDA_OK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
+    try {
+      enqueue_cycle(b, b->cap_stream);
+    } catch (...) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(b->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_OK(cudaStreamEndCapture(b->cap_stream, &g));
+    b->graph_kernels = red_kernel_launches() - before;
+    count_launches((uint64_t)0 - b->graph_kernels);   // captured, not yet executed
+    cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_OK(e);
+  }
+}
+
+void run_cycle(red_batch_s *b, cudaStream_t s) {
+  if (b->graph) {
+    CUDA_OK(cudaGraphLaunch(b->graph, s));
+    count_launches(b->graph_kernels);
+  } else {
+    enqueue_cycle(b, s);
+  }
+}
+
+}  // namespace
+
+red_batch_s *batch_new(const red_problem *problems, int n) {
+  CHECK_ARG(problems != nullptr && n >= 1, "empty batch");
+  std::unique_ptr<red_batch_s> b(new red_batch_s());
+  for (int i = 0; i < n; ++i) {
+    CHECK_ARG(problems[i] != nullptr, "null problem in batch");
+    b->probs.push_back(problems[i]);
+  }
+  const red_config &c0 = b->probs[0]->cfg;
+  b->ve = c0.ve;
+  b->k = c0.ve_k;
+  b->m = c0.ve_m;
+  for (auto *p : b->probs)
+    CHECK_ARG(p->cfg.ve == b->ve && p->cfg.ve_k == b->k && p->cfg.ve_m == b->m,
+              "all problems of a batch need the same ve, ve_k and ve_m");
+  for (auto *p : b->probs) b->pds.push_back(p->pd);
+  CUDA_OK(cudaMalloc(&b->d_pds, sizeof(ProbDev) * n));
+  CUDA_OK(cudaMalloc(&b->d_states, sizeof(ProbState) * n));
+  CUDA_OK(cudaMemset(b->d_states, 0, sizeof(ProbState) * n));
+  CUDA_OK(cudaMalloc(&b->d_ptrs, sizeof(float *) * 2 * n));
+  CUDA_OK(cudaMallocHost(&b->h_states, sizeof(ProbState) * n));
+  CUDA_OK(cudaMallocHost(&b->h_ptrs, sizeof(float *) * 2 * n));
+  b->ops = cycle_ops(b->ve, b->k, b->m);
+  b->fp_per_cycle = 0;
+  for (auto &op : b->ops) b->fp_per_cycle += op.kind == 0;
+  b->tune_key = tune_key(b.get());
+  return b.release();
+}
+
+red_status batch_solve_impl(red_batch_s *b, const void *const *x0, int max_calls, double tol,
+                            void *const *xout, red_stats *stats, cudaStream_t s) {
+  CHECK_ARG(b && x0 && xout, "null argument");
+  CHECK_ARG(max_calls >= 0, "max_fp_calls must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n = (int)b->probs.size();
+  for (int i = 0; i < n; ++i) CHECK_ARG(x0[i] && xout[i], "null image pointer");
+  ensure_ready(b, s);
+  for (int i = 0; i < n; ++i) {
+    b->h_ptrs[i] = const_cast<float *>(static_cast<const float *>(x0[i]));
+    b->h_ptrs[n + i] = static_cast<float *>(xout[i]);
+    ProbState &st = b->h_states[i];
+    std::memset(&st, 0, sizeof(st));
+    st.max_calls = max_calls;
+    st.tol = tol;
+    st.done = max_calls <= 0 ? 1 : 0;
+  }
+  CUDA_OK(cudaMemcpyAsync(b->d_ptrs, b->h_ptrs, sizeof(float *) * 2 * n, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(b->d_states, b->h_states, sizeof(ProbState) * n, cudaMemcpyHostToDevice, s));
+  CUDA_OK(launch_copy_slots(b->d_pds, b->plan.d_items + b->plan.off_chunks, b->plan.n_chunks, 0, 0,
+                            b->d_ptrs, s));
+  const int max_cycles = max_calls <= 0 ? 0 : (max_calls + b->fp_per_cycle - 1) / b->fp_per_cycle;
+  for (int c = 0; c < max_cycles; ++c) {
+    run_cycle(b, s);
+    if (tol > 0.0 && c + 1 < max_cycles) {
+      CUDA_OK(cudaMemcpyAsync(b->h_states, b->d_states, sizeof(ProbState) * n, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int i = 0; i < n; ++i) all = all && b->h_states[i].done;
+      if (all) break;
+    }
+  }
+  CUDA_OK(launch_copy_slots(b->d_pds, b->plan.d_items + b->plan.off_chunks, b->plan.n_chunks, 1, 0,
+                            b->d_ptrs + n, s));
+  CUDA_OK(cudaMemcpyAsync(b->h_states, b->d_states, sizeof(ProbState) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  red_status ret = RED_OK;
+  for (int i = 0; i < n; ++i) {
+    const ProbState &st = b->h_states[i];
+    if (tol > 0.0 && !st.converged) ret = RED_ENOT_CONVERGED;
+    if (stats) {
+      stats[i].fp_calls = st.calls;
+      stats[i].ve_steps = st.ve_steps;
+      stats[i].ve_breakdowns = st.ve_breakdowns;
+      stats[i].converged = st.converged;
+      stats[i].rel_change = st.rel_change;
+      stats[i].sum_abs_gamma = st.sum_abs_gamma;
+      stats[i].ms_total = ms;
+    }
+  }
+  return ret;
+}
+
+}  // namespace red
+
+extern "C" {
+
+red_status red_batch_create(const red_problem *problems, int n, red_batch *out) {
+  return guarded([&] {
+    CHECK_ARG(out != nullptr, "null output");
+    *out = batch_new(problems, n);
+    return RED_OK;
+  });
+}
+
+red_status red_batch_destroy(red_batch b) {
+  return guarded([&] {
+    delete b;
+    return RED_OK;
+  });
+}
+
+red_status red_batch_solve(red_batch b, const void *const *x0_dev, int max_fp_calls,
+                           double rel_tol, void *const *x_out_dev, red_stats *stats,
+                           void *stream) {
+  return guarded([&] {
+    return batch_solve_impl(b, x0_dev, max_fp_calls, rel_tol, x_out_dev, stats,
+                            static_cast<cudaStream_t>(stream));
+  });
+}
+
+red_status red_batch_set_phase_timing(red_batch b, int enable) {
+  return guarded([&] {
+    CHECK_ARG(b != nullptr, "null batch");
+    if (b->phase_timing != (enable != 0)) {
+      b->phase_timing = enable != 0;
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+    }
+    return RED_OK;
+  });
+}
+
+red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launches) {
+  return guarded([&] {
+    CHECK_ARG(b != nullptr && avg_ms != nullptr, "null argument");
+    double sum = 0.0;
+    int cnt = 0;
+    for (auto &e : b->phase_events) {
+      if (e.phase != phase) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      sum += ms;
+      ++cnt;
+    }
+    *avg_ms = cnt ? sum / cnt : 0.0;
+    if (launches) *launches = cnt;
+    return RED_OK;
+  });
+}
+
+red_status red_solve(red_problem p, const void *x0_dev, int max_fp_calls, double rel_tol,
+                     void *x_out_dev, red_stats *stats, void *stream) {
+  return guarded([&] {
+    CHECK_ARG(p != nullptr, "null problem");
+    if (!p->own_batch) {
+      red_problem one = p;
+      p->own_batch = batch_new(&one, 1);
+    }
+    const void *x0[1] = {x0_dev};
+    void *xo[1] = {x_out_dev};
+    return batch_solve_impl(p->own_batch, x0, max_fp_calls, rel_tol, xo, stats,
+                            static_cast<cudaStream_t>(stream));
+  });
+}
+
+red_status red_batch_solve_host(red_batch b, const float *const *y_host,
+                                const float *const *x0_host, int max_fp_calls, double rel_tol,
+                                float *const *x_out_host, red_stats *stats, void *stream) {
+  return guarded([&] {
+    CHECK_ARG(b && x0_host && x_out_host, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = (int)b->probs.size();
+    std::vector<const void *> x0(n);
+    std::vector<void *> xo(n);
+    for (int i = 0; i < n; ++i) {
+      red_problem_s *p = b->probs[i];
+      char *blk = static_cast<char *>(p->block);
+      if (y_host) {
+        CHECK_ARG(y_host[i] != nullptr, "null y");
+        const size_t ny = (size_t)p->pd.lh * p->pd.lw;
+        CUDA_OK(cudaMemcpyAsync(blk + p->L.y, y_host[i], ny * 4, cudaMemcpyHostToDevice, s));
+      }
+      // stage x0 in the problem's scratch buffer; the result comes back through it too
+      float *tmp = reinterpret_cast<float *>(blk + p->L.tmp);
+      CUDA_OK(cudaMemcpyAsync(tmp, x0_host[i], (size_t)p->pd.N * 4, cudaMemcpyHostToDevice, s));
+      x0[i] = tmp;
+      xo[i] = tmp;
+    }
+    if (y_host)
+      for (int i = 0; i < n; ++i) problem_precompute(b->probs[i], s);
+    red_status st = batch_solve_impl(b, x0.data(), max_fp_calls, rel_tol, xo.data(), stats, s);
+    for (int i = 0; i < n; ++i) {
+      red_problem_s *p = b->probs[i];
+      CUDA_OK(cudaMemcpyAsync(x_out_host[i], xo[i], (size_t)p->pd.N * 4, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_OK(cudaStreamSynchronize(s));
+    return st;
+  });
+}
+
+}  // extern "C"

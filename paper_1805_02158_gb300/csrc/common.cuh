@@ -1,0 +1,167 @@
+// Internal declarations shared by the libred translation units (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace red {
+
+constexpr int kMaxK = 16;                       // largest ve_k (columns of U)
+constexpr int kMaxPairs = kMaxK * (kMaxK + 1) / 2;
+constexpr int kGramChunk = 16384;               // pixels per Gram / combine work unit
+constexpr int kNlmR = 8;                        // output rows per NLM thread
+constexpr int kNlmTW = 60;                      // output columns per NLM warp (64 - 4 halo)
+constexpr double kRankTol = 1e-12;              // rank-loss threshold on r_jj^2 / ||u_j||^2
+constexpr double kSumTol = 1e-12;               // MPE existence: |sum c| > tol * sum |c|
+
+enum Task { kDeblur = 0, kSR = 1 };
+enum Ve { kVeNone = 0, kVeMpe = 1, kVeRre = 2, kVeSvdMpe = 3 };
+
+// Per-problem termination state, device resident; written by the step kernels.
+struct ProbState {
+  int done;            // 1 once the solve of this problem has terminated
+  int calls;           // FP steps taken
+  int final_slot;      // ring slot holding the result once done
+  int converged;       // 1 if terminated by the relative-change test
+  int ve_steps;
+  int ve_breakdowns;
+  int max_calls;
+  int ve_status;       // last extrapolation: 0 ok, 1 breakdown
+  double tol;
+  double rel_change;
+  double sum_abs_gamma;
+  unsigned int counter;   // arrival counter for last-block reductions
+  unsigned int counter2;
+};
+
+// Everything a kernel needs to know about one problem. Plain data, copied to device
+// tables; one table per launch group (single problem or batch).
+struct ProbDev {
+  int H, W, M, Wh, N;     // image size; M = W/2; Wh = M + 1; N = H*W
+  int slot_stride;        // elements between ring slots (multiple of 64)
+  int task, scale, lh, lw;
+  int storage;            // 0 = f32 ring, 1 = bf16 ring
+  int nslots;
+  int n_row_items;        // CTAs of one row-FFT launch for this problem
+  int n_chunks;           // Gram / combine work units
+  int kh, kw;             // SR blur size
+  int cg_iters;
+  int ve_k;
+  int ve_method;
+  float inv_sigma2, alpha;
+  float nlm_k;            // NLM prescale sqrt(log2(e) / (P^2 h^2))
+  void *ring;             // nslots * slot_stride elements (float or bf16)
+  float *f;               // denoiser output, N
+  float2 *spec;           // H x Wh half spectrum workspace (deblur)
+  const float2 *Kh;       // H x Wh: K, the PSF spectrum (for H x in the objective)
+  const float2 *Cc;       // H x Wh: conj(K) Y / (sigma^2 D) / (H W)
+  const float *Gg;        // H x Wh: alpha / D / (H W)
+  const float2 *tw_m;     // e^{-2 pi i t / M}, t < M
+  const float2 *tw_w;     // e^{-2 pi i t / W}, t <= M
+  const float2 *tw_h;     // e^{-2 pi i t / H}, t < H
+  float2 *row_stats;      // H partial sums (sum d^2, sum x^2) of one FP step
+  // SR
+  const float *b0;        // H^T y / sigma^2 (N)
+  float *cg_x, *cg_r, *cg_p, *cg_ap, *cg_z;   // CG vectors; z is LR sized
+  const float *psf;       // kh x kw taps
+  // extrapolation
+  double *gram_part;      // n_chunks x kMaxPairs
+  double *ve_coef;        // kMaxK: xi_j of Algorithm 1 step 3 (difference form), + gamma
+  double *gamma;          // kMaxK
+  ProbState *st;
+};
+
+struct Item {             // one CTA's work unit
+  int prob;
+  int a, b, c;
+};
+
+// Which ring slots a launch reads and writes, or explicit pointers (single-problem calls).
+struct StepArgs {
+  int src, dst;           // ring slots
+  const void *src_ptr;    // if non-null: read this instead of slot src (f32)
+  float *dst_ptr;         // if non-null: write this instead of slot dst (f32)
+  int update_state;       // 1: batched solve step (skip done problems, count calls)
+};
+
+struct VeArgs {
+  int slots[kMaxK + 1];   // ring slots of x_m .. x_{m+k}
+  const float *ptrs[kMaxK + 1];  // explicit vectors (single-problem call) or null
+  float *out_ptr;         // explicit output or null
+  int out_slot;
+  int nvec;               // k + 1
+  int update_state;
+};
+
+// ---- host-side launch helpers (defined in the .cu files) -------------------------------
+struct LaunchCfg {
+  int nlm_wy = 4;          // warps per NLM CTA (tile height = 8 * nlm_wy rows)
+  int fft_rows = 0;        // rows per row-FFT CTA (0 = auto from the row length)
+  int fft_cols = 0;        // columns per column-FFT CTA (0 = auto from the column length)
+  int sr_cluster = 8;      // CTAs per super-resolution cluster (one cluster per problem)
+};
+
+cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
+                       StepArgs sa, int src_is_bf16, cudaStream_t s);
+// FFT launches: items carry (prob, first row/col, count). tw_cap = largest transform
+// length in the launch (M for rows, H for columns); buf_cap = largest per-item buffer
+// (rows * M, or cols * (H + 1)) in complex elements.
+cudaError_t launch_fft_r2c(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           int tw_cap, int buf_cap, const float *src_override,
+                           float2 *dst_override, int skip_done, cudaStream_t s);
+cudaError_t launch_fft_cols(const ProbDev *d_probs, const Item *d_items, int n_items,
+                            int tw_cap, int buf_cap, int mode, float2 *spec_override,
+                            int skip_done, cudaStream_t s);
+cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           int tw_cap, int buf_cap, StepArgs sa, cudaStream_t s);
+cudaError_t launch_spectral_constants(const ProbDev *d_prob, const float2 *k_hat,
+                                      const float2 *y_hat, float2 *Cc, float *Gg, int n,
+                                      double inv_sigma2, double alpha, double inv_hw,
+                                      cudaStream_t s);
+cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items,
+                        const VeArgs &va, cudaStream_t s);
+cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec,
+                            int update_state, cudaStream_t s);
+cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           const VeArgs &va, cudaStream_t s);
+cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n_items,
+                              int mode, int slot, float *const *d_ptrs, cudaStream_t s);
+cudaError_t launch_sr_rhs(const ProbDev *d_prob, const float *y, cudaStream_t s);
+cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_sr,
+                           int cluster, StepArgs sa, cudaStream_t s);
+cudaError_t launch_objective(const ProbDev *d_prob, const float *x, const float *hx,
+                             const float *y, const float *f, double *out, cudaStream_t s);
+
+int fft_smem_rows(int tw_cap, int buf_cap);
+int fft_smem_cols(int tw_cap, int buf_cap);
+
+void count_launches(uint64_t n);
+cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col_buf_cap);
+cudaError_t sr_prepare(int cluster);
+cudaError_t nlm_prepare(int wy);
+
+// ---- small device helpers ---------------------------------------------------------------
+__host__ __device__ __forceinline__ int mirror_index(int i, int n) {
+  // half-sample symmetric reflection into [0, n), period 2n
+  int p = 2 * n;
+  i %= p;
+  if (i < 0) i += p;
+  return i < n ? i : p - 1 - i;
+}
+
+__device__ __forceinline__ float load_img(const void *base, long idx, int is_bf16) {
+  if (is_bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
+  return reinterpret_cast<const float *>(base)[idx];
+}
+
+__device__ __forceinline__ void store_img(void *base, long idx, float v, int is_bf16) {
+  if (is_bf16)
+    reinterpret_cast<__nv_bfloat16 *>(base)[idx] = __float2bfloat16_rn(v);
+  else
+    reinterpret_cast<float *>(base)[idx] = v;
+}
+
+}  // namespace red

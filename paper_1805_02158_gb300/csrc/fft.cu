@@ -1,0 +1,390 @@
+// Fourier-domain linear solve of the FP step for a block-circulant blur H (Eq. (7) and
+// its footnote): x_{k+1} = IFFT2( C + G . FFT2(f) ),
+//   C = conj(K) FFT2(y) / (sigma^2 D) / (H W),  G = alpha / D / (H W),
+//   D = |K|^2 / sigma^2 + alpha,  K = FFT2 of the circularly centred PSF.
+//
+// The 2-D transform is three passes over a half spectrum (H x (W/2 + 1) complex):
+//   1. rows, real-to-complex: each row of W reals is packed as W/2 complex values, a
+//      W/2-point complex FFT is taken and the W/2 + 1 non-redundant bins are untangled;
+//   2. columns: forward FFT of each column, the pointwise solve X = C + G F, inverse FFT
+//      (all in shared memory, one read and one write of the spectrum);
+//   3. rows, complex-to-real, with the relative-change statistics of the FP step
+//      (sum (x_{k+1} - x_k)^2, sum x_k^2) reduced on the fly and, in a batched solve, the
+//      termination test of the problem done by the last CTA to finish it.
+// Transforms are self-sorting Stockham passes in shared memory with radix 4, 2 and 3
+// (sizes 2^a 3^b), twiddles from tables computed on the host in double precision.
+// Inverse transforms use IFFT(X) = conj(FFT(conj(X))); the 1/(H W) scale is folded
+// into C and G.
+#include "common.cuh"
+
+namespace red {
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // * (-i)
+__device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); }  // * (+i)
+
+// Forward Stockham FFT of `nseq` sequences of length n held in shared memory (sequence s
+// at x + s * ss). Ping-pongs between x and y; returns the buffer holding the result.
+// Pass with radix r after previous passes of product Ns: butterfly j reads elements
+// j + q n/r, twiddles them by w_n^{(j mod Ns) q n/(Ns r)}, takes an r-point DFT and writes
+// to (j - j mod Ns) r + j mod Ns + q Ns (natural order output).
+__device__ float2 *stockham(float2 *x, float2 *y, int n, int nseq, int ss,
+                            const float2 *__restrict__ tw, int tid, int nthr) {
+  float2 *in = x, *out = y;
+  int Ns = 1;
+  int rem = n;
+  while (rem > 1) {
+    const int r = (rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3);
+    const int nb = n / r;
+    const int tws = n / (Ns * r);
+    const int total = nseq * nb;
+    for (int t = tid; t < total; t += nthr) {
+      const int s = t / nb;
+      const int j = t - s * nb;
+      const float2 *src = in + s * ss;
+      float2 *dst = out + s * ss;
+      const int kk = j % Ns;
+      const int base = (j - kk) * r + kk;
+      if (r == 4) {
+        float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb], a3 = src[j + 3 * nb];
+        if (kk) {
+          a1 = cmul(a1, tw[kk * tws]);
+          a2 = cmul(a2, tw[2 * kk * tws]);
+          a3 = cmul(a3, tw[3 * kk * tws]);
+        }
+        const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+        const float2 t3 = mul_mi(csub(a1, a3));
+        dst[base] = cadd(t0, t2);
+        dst[base + Ns] = cadd(t1, t3);
+        dst[base + 2 * Ns] = csub(t0, t2);
+        dst[base + 3 * Ns] = csub(t1, t3);
+      } else if (r == 2) {
+        float2 a0 = src[j], a1 = src[j + nb];
+        if (kk) a1 = cmul(a1, tw[kk * tws]);
+        dst[base] = cadd(a0, a1);
+        dst[base + Ns] = csub(a0, a1);
+      } else {
+        float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb];
+        if (kk) {
+          a1 = cmul(a1, tw[kk * tws]);
+          a2 = cmul(a2, tw[2 * kk * tws]);
+        }
+        // w = e^{-2 pi i / 3}: y1 = a0 - s/2 - i (sqrt3/2) d, y2 = a0 - s/2 + i (sqrt3/2) d
+        const float2 s12 = cadd(a1, a2), d12 = csub(a1, a2);
+        const float2 m = make_float2(a0.x - 0.5f * s12.x, a0.y - 0.5f * s12.y);
+        const float h = 0.86602540378443864676f;
+        const float2 e = make_float2(h * d12.x, h * d12.y);
+        dst[base] = cadd(a0, s12);
+        dst[base + Ns] = cadd(m, mul_mi(e));
+        dst[base + 2 * Ns] = cadd(m, mul_pi(e));
+      }
+    }
+    __syncthreads();
+    float2 *tmp = in;
+    in = out;
+    out = tmp;
+    Ns *= r;
+    rem /= r;
+  }
+  return in;
+}
+
+// Pass 1: rows, real to half spectrum. Item (prob, first row).
+__global__ void __launch_bounds__(256)
+k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
+          int buf_cap, const float *src_override, float2 *dst_override, int skip_done) {
+  extern __shared__ float2 sm[];
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (skip_done && P->st->done) return;
+  const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
+  const int r0 = it.a;
+  const int nr = min(it.b, H - r0);
+  float2 *twm = sm;
+  float2 *tww = twm + tw_cap;
+  float2 *b0 = tww + tw_cap + 1;
+  float2 *b1 = b0 + buf_cap;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
+  for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
+  const float *src = src_override ? src_override : P->f;
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    const int row = idx / M, n = idx - row * M;
+    b0[row * M + n] = reinterpret_cast<const float2 *>(src + (long)(r0 + row) * W)[n];
+  }
+  __syncthreads();
+  const float2 *Z = stockham(b0, b1, M, nr, M, twm, tid, nthr);
+  float2 *dst = dst_override ? dst_override : P->spec;
+  for (int idx = tid; idx < nr * Wh; idx += nthr) {
+    const int row = idx / Wh, kk = idx - row * Wh;
+    const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
+    const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
+    // X_k = ((Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k})) / 2
+    const float2 t = cmul(tww[kk], csub(zk, zc));
+    const float2 sum = cadd(zk, zc);
+    dst[(long)(r0 + row) * Wh + kk] = make_float2(0.5f * (sum.x + t.y), 0.5f * (sum.y - t.x));
+  }
+}
+
+// Pass 2: columns of the half spectrum. mode 0: forward FFT only (spectra of y and the
+// PSF at set-up); mode 1: forward FFT, X = C + G F, inverse FFT (the FP-step solve);
+// mode 2: forward FFT, X = K F / (H W), inverse FFT (H x, for the objective).
+__global__ void __launch_bounds__(256)
+k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
+           int buf_cap, int mode, float2 *spec_override, int skip_done) {
+  extern __shared__ float2 sm[];
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (skip_done && P->st->done) return;
+  const int H = P->H, Wh = P->Wh;
+  const int c0 = it.a;
+  const int nc = min(it.b, Wh - c0);
+  const int hs = H + 1;   // padded column stride in shared memory
+  float2 *twh = sm;
+  float2 *b0 = twh + tw_cap;
+  float2 *b1 = b0 + buf_cap;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
+  float2 *spec = spec_override ? spec_override : P->spec;
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    const int r = idx / nc, c = idx - r * nc;
+    b0[c * hs + r] = spec[(long)r * Wh + c0 + c];
+  }
+  __syncthreads();
+  float2 *F = stockham(b0, b1, H, nc, hs, twh, tid, nthr);
+  if (mode == 0) {
+    for (int idx = tid; idx < H * nc; idx += nthr) {
+      const int r = idx / nc, c = idx - r * nc;
+      spec[(long)r * Wh + c0 + c] = F[c * hs + r];
+    }
+    return;
+  }
+  if (mode == 1) {
+    for (int idx = tid; idx < H * nc; idx += nthr) {
+      const int r = idx / nc, c = idx - r * nc;
+      const long g = (long)r * Wh + c0 + c;
+      const float2 cc = P->Cc[g];
+      const float gg = P->Gg[g];
+      const float2 f = F[c * hs + r];
+      F[c * hs + r] = make_float2(fmaf(gg, f.x, cc.x), -fmaf(gg, f.y, cc.y));  // conj(C + G F)
+    }
+  } else {
+    // mode 2: H x for the objective: conj(K F / (H W))
+    const float inv_hw = 1.0f / ((float)H * (float)P->W);
+    for (int idx = tid; idx < H * nc; idx += nthr) {
+      const int r = idx / nc, c = idx - r * nc;
+      const float2 kk = P->Kh[(long)r * Wh + c0 + c];
+      const float2 v = cmul(kk, F[c * hs + r]);
+      F[c * hs + r] = make_float2(v.x * inv_hw, -v.y * inv_hw);
+    }
+  }
+  __syncthreads();
+  float2 *other = (F == b0) ? b1 : b0;
+  const float2 *X = stockham(F, other, H, nc, hs, twh, tid, nthr);
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    const int r = idx / nc, c = idx - r * nc;
+    spec[(long)r * Wh + c0 + c] = cconj(X[c * hs + r]);
+  }
+}
+
+// Pass 3: rows, half spectrum to real, with the FP-step statistics.
+__global__ void __launch_bounds__(256)
+k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
+          int buf_cap, StepArgs sa) {
+  extern __shared__ float2 sm[];
+  __shared__ int is_last;
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (sa.update_state && P->st->done) return;
+  const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
+  const int r0 = it.a;
+  const int nr = min(it.b, H - r0);
+  float2 *twm = sm;
+  float2 *tww = twm + tw_cap;
+  float2 *b0 = tww + tw_cap + 1;
+  float2 *b1 = b0 + buf_cap;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
+  for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
+  __syncthreads();
+  const float2 *spec = P->spec;
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    const int row = idx / M, kk = idx - row * M;
+    const float2 xk = spec[(long)(r0 + row) * Wh + kk];
+    const float2 xc = cconj(spec[(long)(r0 + row) * Wh + (M - kk)]);
+    // 2 E_k = X_k + conj X_{M-k};  2 O_k = (X_k - conj X_{M-k}) e^{+2 pi i k / W}
+    const float2 e = cadd(xk, xc);
+    const float2 o = cmul(csub(xk, xc), cconj(tww[kk]));
+    const float2 z = cadd(e, mul_pi(o));          // 2 Z_k = 2 E_k + i 2 O_k
+    b0[row * M + kk] = cconj(z);
+  }
+  __syncthreads();
+  const float2 *Y = stockham(b0, b1, M, nr, M, twm, tid, nthr);
+
+  // output row = conj(Y); x[2n] = Re, x[2n+1] = Im; statistics against x_in
+  const int esz = P->storage ? 2 : 4;
+  float *dst = sa.dst_ptr ? sa.dst_ptr : nullptr;
+  void *dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
+  const void *src_ring = sa.src_ptr ? sa.src_ptr
+                                    : static_cast<const char *>(P->ring) +
+                                          (size_t)sa.src * P->slot_stride * esz;
+  const int src_bf16 = sa.src_ptr ? 0 : P->storage;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  for (int row = warp; row < nr; row += nwarps) {
+    const long rowbase = (long)(r0 + row) * W;
+    float sd = 0.f, sx = 0.f;
+    for (int n = lane; n < M; n += 32) {
+      const float2 v = Y[row * M + n];
+      const float xe = v.x, xo = -v.y;
+      if (dst) {
+        reinterpret_cast<float2 *>(dst + rowbase)[n] = make_float2(xe, xo);
+      } else {
+        store_img(dst_ring, rowbase + 2 * n, xe, P->storage);
+        store_img(dst_ring, rowbase + 2 * n + 1, xo, P->storage);
+      }
+      // statistics use the stored (rounded) values of the new iterate
+      const float ye = P->storage ? __bfloat162float(__float2bfloat16_rn(xe)) : xe;
+      const float yo = P->storage ? __bfloat162float(__float2bfloat16_rn(xo)) : xo;
+      const float pe = load_img(src_ring, rowbase + 2 * n, src_bf16);
+      const float po = load_img(src_ring, rowbase + 2 * n + 1, src_bf16);
+      sd = fmaf(ye - pe, ye - pe, sd);
+      sd = fmaf(yo - po, yo - po, sd);
+      sx = fmaf(pe, pe, sx);
+      sx = fmaf(po, po, sx);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sd += __shfl_xor_sync(0xffffffffu, sd, off);
+      sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    }
+    if (lane == 0) P->row_stats[r0 + row] = make_float2(sd, sx);
+  }
+  if (!sa.update_state) return;
+
+  // last CTA of this problem: fixed-order reduction of the row sums, termination test
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&P->st->counter, 1u);
+    is_last = (t == (unsigned)(P->n_row_items - 1));
+  }
+  __syncthreads();
+  if (!is_last || warp != 0) return;
+  __threadfence();
+  double sd = 0.0, sx = 0.0;
+  for (int r = lane; r < H; r += 32) {
+    const float2 v = __ldcg(&P->row_stats[r]);
+    sd += (double)v.x;
+    sx += (double)v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sd += __shfl_xor_sync(0xffffffffu, sd, off);
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+  }
+  if (lane == 0) {
+    ProbState *st = P->st;
+    const double rel = sx > 0.0 ? sqrt(sd / sx) : (sd > 0.0 ? INFINITY : 0.0);
+    st->rel_change = rel;
+    st->calls += 1;
+    if (rel < st->tol || st->calls >= st->max_calls) {
+      st->done = 1;
+      st->converged = rel < st->tol ? 1 : 0;
+      st->final_slot = sa.dst;
+    }
+    st->counter = 0;
+    __threadfence();
+  }
+}
+
+__global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,
+                                     float2 *Cc, float *Gg, int n, double inv_sigma2,
+                                     double alpha, double inv_hw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double kr = khat[i].x, ki = khat[i].y;
+  const double yr = yhat[i].x, yi = yhat[i].y;
+  const double d = (kr * kr + ki * ki) * inv_sigma2 + alpha;
+  // conj(K) Y = (kr yr + ki yi) + i (kr yi - ki yr)
+  const double s = inv_sigma2 / d * inv_hw;
+  Cc[i] = make_float2((float)((kr * yr + ki * yi) * s), (float)((kr * yi - ki * yr) * s));
+  Gg[i] = (float)(alpha / d * inv_hw);
+}
+
+}  // namespace
+
+int fft_smem_rows(int tw_cap, int buf_cap) { return (int)((2 * (size_t)tw_cap + 1 + 2 * (size_t)buf_cap) * sizeof(float2)); }
+int fft_smem_cols(int tw_cap, int buf_cap) { return (int)(((size_t)tw_cap + 2 * (size_t)buf_cap) * sizeof(float2)); }
+
+// Raises a kernel's dynamic shared-memory limit the first time a launch needs more
+// than the 48 KB default (a per-kernel high-water mark; races only repeat the call).
+static cudaError_t set_smem(const void *fn, int bytes, int *high_water) {
+  if (bytes <= 48 * 1024 || bytes <= *high_water) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) *high_water = bytes;
+  return e;
+}
+static int hw_r2c = 0, hw_cols = 0, hw_c2r = 0;
+
+cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col_buf_cap) {
+  const int sr = fft_smem_rows(row_tw_cap, row_buf_cap), sc = fft_smem_cols(col_tw_cap, col_buf_cap);
+  cudaError_t e = set_smem((const void *)k_fft_r2c, sr, &hw_r2c);
+  if (e == cudaSuccess) e = set_smem((const void *)k_fft_c2r, sr, &hw_c2r);
+  if (e == cudaSuccess) e = set_smem((const void *)k_fft_cols, sc, &hw_cols);
+  return e;
+}
+
+cudaError_t launch_fft_r2c(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           int tw_cap, int buf_cap, const float *src_override,
+                           float2 *dst_override, int skip_done, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int smem = fft_smem_rows(tw_cap, buf_cap);
+  cudaError_t e = set_smem((const void *)k_fft_r2c, smem, &hw_r2c);
+  if (e != cudaSuccess) return e;
+  k_fft_r2c<<<n_items, 256, smem, s>>>(d_probs, d_items, tw_cap, buf_cap, src_override,
+                                       dst_override, skip_done);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_cols(const ProbDev *d_probs, const Item *d_items, int n_items,
+                            int tw_cap, int buf_cap, int mode, float2 *spec_override,
+                            int skip_done, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int smem = fft_smem_cols(tw_cap, buf_cap);
+  cudaError_t e = set_smem((const void *)k_fft_cols, smem, &hw_cols);
+  if (e != cudaSuccess) return e;
+  k_fft_cols<<<n_items, 256, smem, s>>>(d_probs, d_items, tw_cap, buf_cap, mode, spec_override,
+                                        skip_done);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           int tw_cap, int buf_cap, StepArgs sa, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int smem = fft_smem_rows(tw_cap, buf_cap);
+  cudaError_t e = set_smem((const void *)k_fft_c2r, smem, &hw_c2r);
+  if (e != cudaSuccess) return e;
+  k_fft_c2r<<<n_items, 256, smem, s>>>(d_probs, d_items, tw_cap, buf_cap, sa);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectral_constants(const ProbDev *, const float2 *k_hat, const float2 *y_hat,
+                                      float2 *Cc, float *Gg, int n, double inv_sigma2,
+                                      double alpha, double inv_hw, cudaStream_t s) {
+  k_spectral_constants<<<(n + 255) / 256, 256, 0, s>>>(k_hat, y_hat, Cc, Gg, n, inv_sigma2,
+                                                       alpha, inv_hw);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace red

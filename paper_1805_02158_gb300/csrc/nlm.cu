@@ -1,0 +1,177 @@
+// Non-local-means denoiser f(x): the denoising engine called once per FP step (Eq. (7)),
+// the dominant cost of RED (Sec. II-B: "hundreds of denoising activations").
+//
+// Definition (same as the FP64 oracle): for every pixel p,
+//   f(p) = sum_d w(p,d) xp(p+d) / sum_d w(p,d),  d in [-5,5]^2 (11x11 search window),
+//   w(p,d) = exp(-(1/(25 h^2)) sum_{t in [-2,2]^2} (xp(p+t) - xp(p+d+t))^2),
+// xp = x extended by half-sample symmetric reflection.
+//
+// GB300 mapping. One CTA = a tile of 60 output columns x (8 * warps) output rows; the
+// tile plus a 7-pixel halo (search radius 5 + patch radius 2) is staged once in shared
+// memory, prescaled by k = sqrt(log2(e) / (25 h^2)) so that a weight is a single
+// ex2.approx of a negated patch distance. Each lane owns 2 adjacent columns and 8 rows:
+//   * the lane's own patch rows a(rr) (12 x 2 values) stay in registers for all 121 offsets;
+//   * for each dx the lane loads the 22 candidate rows it needs for all 11 dy once, so
+//     the dy loop (fully unrolled) only renames registers;
+//   * vertical 5-row sums of squared differences slide down the column with 2 FMAs/row;
+//   * horizontal 5-column sums use 4 warp shuffles per row (the warp covers 64 columns
+//     and outputs the inner 60).
+// Per output pixel and offset: ~8.4 FP32 ops, 1 MUFU.EX2, 2 SHFL; no shared-memory
+// traffic in the inner loop beyond one candidate row per dy.
+//
+// Work decomposition is fixed to an (8-row, 2-column) grid in image coordinates, so a
+// pixel's arithmetic (and result, bit for bit) does not depend on the CTA shape chosen
+// by the autotuner or on which other problems share the launch.
+#include "common.cuh"
+
+namespace red {
+
+namespace {
+
+constexpr int kCols = kNlmTW + 14;   // staged columns: [tc0 - 7, tc0 + 67)
+constexpr int kStride = 76;          // shared-memory row stride (floats)
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int R>
+__global__ void __launch_bounds__(128, 3)
+k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArgs sa,
+      int src_is_bf16_override) {
+  extern __shared__ float tile[];
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (sa.update_state && P->st->done) return;
+
+  const int H = P->H, W = P->W;
+  const int tr0 = it.a, tc0 = it.b;
+  const int wy = blockDim.y;
+  const int rows = R * wy + 14;
+  const float k = P->nlm_k;
+
+  const void *src;
+  int bf16;
+  if (sa.src_ptr) {
+    src = sa.src_ptr;
+    bf16 = src_is_bf16_override;
+  } else {
+    bf16 = P->storage;
+    src = static_cast<const char *>(P->ring) +
+          (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
+  }
+
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int nthr = 32 * wy;
+  for (int idx = tid; idx < rows * kCols; idx += nthr) {
+    const int rr = idx / kCols;
+    const int cc = idx - rr * kCols;
+    const int gr = mirror_index(tr0 - 7 + rr, H);
+    const int gc = mirror_index(tc0 - 7 + cc, W);
+    tile[rr * kStride + cc] = k * load_img(src, (long)gr * W + gc, bf16);
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x;
+  const int r0 = threadIdx.y * R;     // warp's first output row, tile-local
+  const int sc0 = 2 * lane + 5;       // staged column of the lane's first column
+
+  // own patch rows: staged rows r0 + 5 .. r0 + R + 8 (output rows r0-2 .. r0+R+1)
+  float a0[R + 4], a1[R + 4];
+#pragma unroll
+  for (int rr = 0; rr < R + 4; ++rr) {
+    a0[rr] = tile[(r0 + 5 + rr) * kStride + sc0];
+    a1[rr] = tile[(r0 + 5 + rr) * kStride + sc0 + 1];
+  }
+  float num0[R], num1[R], den0[R], den1[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) num0[r] = num1[r] = den0[r] = den1[r] = 0.f;
+
+#pragma unroll 1
+  for (int dx = -5; dx <= 5; ++dx) {
+    // candidate rows for dy = -5..5: staged rows r0 .. r0 + R + 13
+    const float *bcol = tile + sc0 + dx;
+    float b0[R + 14], b1[R + 14];
+#pragma unroll
+    for (int t = 0; t < R + 14; ++t) {
+      b0[t] = bcol[(r0 + t) * kStride];
+      b1[t] = bcol[(r0 + t) * kStride + 1];
+    }
+#pragma unroll
+    for (int dyi = 0; dyi < 11; ++dyi) {
+      float d0[R + 4], d1[R + 4];
+#pragma unroll
+      for (int rr = 0; rr < R + 4; ++rr) {
+        d0[rr] = a0[rr] - b0[rr + dyi];
+        d1[rr] = a1[rr] - b1[rr + dyi];
+      }
+      float v0 = d0[0] * d0[0];
+      float v1 = d1[0] * d1[0];
+#pragma unroll
+      for (int t = 1; t < 5; ++t) {
+        v0 = fmaf(d0[t], d0[t], v0);
+        v1 = fmaf(d1[t], d1[t], v1);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (r > 0) {
+          v0 = fmaf(d0[r + 4], d0[r + 4], fmaf(-d0[r - 1], d0[r - 1], v0));
+          v1 = fmaf(d1[r + 4], d1[r + 4], fmaf(-d1[r - 1], d1[r - 1], v1));
+        }
+        const float p = v0 + v1;
+        const float pl = __shfl_up_sync(kFull, p, 1);
+        const float pr = __shfl_down_sync(kFull, p, 1);
+        const float v1l = __shfl_up_sync(kFull, v1, 1);
+        const float v0r = __shfl_down_sync(kFull, v0, 1);
+        const float D0 = (pl + p) + v0r;
+        const float D1 = (v1l + p) + pr;
+        const float w0 = ex2_approx(-D0);
+        const float w1 = ex2_approx(-D1);
+        num0[r] = fmaf(w0, b0[r + 2 + dyi], num0[r]);
+        num1[r] = fmaf(w1, b1[r + 2 + dyi], num1[r]);
+        den0[r] += w0;
+        den1[r] += w1;
+      }
+    }
+  }
+
+  if (lane == 0 || lane == 31) return;  // halo lanes
+  float *dst;
+  if (sa.dst_ptr)
+    dst = sa.dst_ptr;
+  else
+    dst = P->f;
+  const float inv_k = 1.0f / k;
+  const int c = tc0 - 2 + 2 * lane;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gr = tr0 + r0 + r;
+    if (gr >= H) break;
+    if (c < W) dst[(long)gr * W + c] = (num0[r] / den0[r]) * inv_k;
+    if (c + 1 < W) dst[(long)gr * W + c + 1] = (num1[r] / den1[r]) * inv_k;
+  }
+}
+
+}  // namespace
+
+cudaError_t nlm_prepare(int wy) {
+  const int smem = (kNlmR * wy + 14) * kStride * (int)sizeof(float);
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute((const void *)k_nlm<kNlmR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
+                       StepArgs sa, int src_is_bf16, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(kNlmR * wy + 14) * kStride * sizeof(float);
+  dim3 block(32, wy);
+  k_nlm<kNlmR><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace red

@@ -1,0 +1,396 @@
+// Vector extrapolation on the device (Sec. III-B): MPE (Algorithm 1) and RRE (Eq. (19)).
+//
+// From the stored iterates x_m .. x_{m+kappa+1} (K = kappa + 1 differences):
+//   1. k_gram:     G = U^T U, U = [x_{m+1} - x_m, ..., x_{m+K} - x_{m+K-1}], formed on the fly.
+//                  HBM-bound tall-skinny reduction: each work unit (problem, chunk of
+//                  16384 pixels) reads the K + 1 vectors once with 16-byte loads. The
+//                  differences are split exactly (TwoSum: u = s + e), the products are
+//                  exact (TwoProduct with FMA) and accumulated in double-float (hi + lo)
+//                  per thread, then reduced across the CTA in FP64. The result has
+//                  FP64-level accuracy without FP64 arithmetic in the pixel loop (FP64
+//                  throughput on this part is a small fraction of FP32).
+//   2. k_ve_solve: per problem, one thread: sums the chunk partials in a fixed order,
+//                  Cholesky G = R^T R (R is the R of Algorithm 2's QR up to signs), then
+//                  MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2) or
+//                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), all in FP64, with
+//                  the rank-loss and existence rules of the oracle.
+//   3. k_combine:  Algorithm 1 steps 3-4 evaluated without Q as
+//                  x_(m,kappa) = x_m + U_{kappa-1} xi (= x_m + Q_{kappa-1} R_{kappa-1} xi),
+//                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
+// Chunks are fixed per problem, so the reduction order (and the result) does not depend
+// on the launch shape or on other problems in the batch.
+#include "common.cuh"
+
+namespace red {
+
+namespace {
+
+__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e) {
+  s = __fsub_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+}
+
+__device__ __forceinline__ const float *vec_ptr(const ProbDev *P, const VeArgs &va, int i) {
+  if (va.ptrs[i]) return va.ptrs[i];
+  return static_cast<const float *>(P->ring) + (size_t)va.slots[i] * P->slot_stride;
+}
+
+__device__ __forceinline__ const __nv_bfloat16 *vec_ptr_bf16(const ProbDev *P, const VeArgs &va, int i) {
+  return static_cast<const __nv_bfloat16 *>(P->ring) + (size_t)va.slots[i] * P->slot_stride;
+}
+
+template <int K>
+struct GramAcc {
+  float hi[K * (K + 1) / 2];
+  float lo[K * (K + 1) / 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < K * (K + 1) / 2; ++i) hi[i] = lo[i] = 0.f;
+  }
+  // one pixel: x[0..K]
+  __device__ __forceinline__ void add(const float (&x)[K + 1]) {
+    float s[K], e[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) two_diff(x[i + 1], x[i], s[i], e[i]);
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+#pragma unroll
+      for (int j = i; j < K; ++j) {
+        const float p = __fmul_rn(s[i], s[j]);
+        const float pe = __fmaf_rn(s[i], s[j], -p);
+        const float cross = __fmaf_rn(s[i], e[j], __fmul_rn(e[i], s[j]));
+        // TwoSum(hi, p)
+        const float h = hi[idx];
+        const float t = __fadd_rn(h, p);
+        const float z = __fsub_rn(t, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, z)), __fsub_rn(p, z));
+        hi[idx] = t;
+        lo[idx] = __fadd_rn(lo[idx], __fadd_rn(err, __fadd_rn(pe, cross)));
+        ++idx;
+      }
+    }
+  }
+};
+
+template <int K>
+__global__ void __launch_bounds__(256)
+k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
+  constexpr int NP = K * (K + 1) / 2;
+  __shared__ double red[8][NP];
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (va.update_state && P->st->done) return;
+  const int N = P->N;
+  const int begin = it.a * kGramChunk;
+  const int end = min(N, begin + kGramChunk);
+  GramAcc<K> acc;
+  acc.zero();
+  const int tid = threadIdx.x;
+  const bool bf16 = (va.ptrs[0] == nullptr) && P->storage;
+  if (!bf16) {
+    const float *xp[K + 1];
+#pragma unroll
+    for (int i = 0; i <= K; ++i) xp[i] = vec_ptr(P, va, i);
+    bool aligned = ((begin & 3) == 0);
+#pragma unroll
+    for (int i = 0; i <= K; ++i) aligned = aligned && ((reinterpret_cast<uintptr_t>(xp[i]) & 15) == 0);
+    int p0 = begin;
+    if (aligned) {
+      const int nv = (end - begin) >> 2;
+      for (int v = tid; v < nv; v += blockDim.x) {
+        float4 q[K + 1];
+#pragma unroll
+        for (int i = 0; i <= K; ++i) q[i] = __ldcs(reinterpret_cast<const float4 *>(xp[i] + begin) + v);
+        float x[K + 1];
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].x;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].y;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].z;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].w;
+        acc.add(x);
+      }
+      p0 = begin + (nv << 2);
+    }
+    for (int p = p0 + tid; p < end; p += blockDim.x) {
+      float x[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) x[i] = xp[i][p];
+      acc.add(x);
+    }
+  } else {
+    const __nv_bfloat16 *xp[K + 1];
+#pragma unroll
+    for (int i = 0; i <= K; ++i) xp[i] = vec_ptr_bf16(P, va, i);
+    for (int p = begin + tid; p < end; p += blockDim.x) {
+      float x[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) x[i] = __bfloat162float(xp[i][p]);
+      acc.add(x);
+    }
+  }
+  // CTA reduction in FP64, fixed order
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    double v = (double)acc.hi[q] + (double)acc.lo[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < NP) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][tid];
+    P->gram_part[(size_t)it.a * kMaxPairs + tid] = v;
+  }
+}
+
+// Generic FP64 path for K > 10 (rarely used; correct but not tuned).
+__global__ void __launch_bounds__(256)
+k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
+  __shared__ double red[kMaxPairs];
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (va.update_state && P->st->done) return;
+  const int K = va.nvec - 1;
+  const int NP = K * (K + 1) / 2;
+  const int begin = it.a * kGramChunk;
+  const int end = min(P->N, begin + kGramChunk);
+  for (int q = threadIdx.x; q < NP; q += blockDim.x) red[q] = 0.0;
+  __syncthreads();
+  // thread t accumulates pair q = t mod NP over a strided subset of pixels, then atomics
+  // are avoided by a fixed two-level order: each thread owns one pair.
+  for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+    int i = 0, rem = q;
+    while (rem >= K - i) { rem -= K - i; ++i; }
+    const int j = i + rem;
+    double s = 0.0;
+    for (int p = begin; p < end; ++p) {
+      const float *xi0 = vec_ptr(P, va, i), *xi1 = vec_ptr(P, va, i + 1);
+      const float *xj0 = vec_ptr(P, va, j), *xj1 = vec_ptr(P, va, j + 1);
+      const double ui = (double)xi1[p] - (double)xi0[p];
+      const double uj = (double)xj1[p] - (double)xj0[p];
+      s += ui * uj;
+    }
+    red[q] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NP; q += blockDim.x)
+    P->gram_part[(size_t)it.a * kMaxPairs + q] = red[q];
+}
+
+// Upper-triangular solve R x = b (k x k, row-major with stride kMaxK).
+__device__ void back_sub(const double *R, const double *b, double *x, int k) {
+  for (int i = k - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < k; ++j) s -= R[i * kMaxK + j] * x[j];
+    x[i] = s / R[i * kMaxK + i];
+  }
+}
+
+// R^T z = b (forward substitution with the transpose of upper-triangular R).
+__device__ void fwd_sub_t(const double *R, const double *b, double *z, int k) {
+  for (int i = 0; i < k; ++i) {
+    double s = b[i];
+    for (int j = 0; j < i; ++j) s -= R[j * kMaxK + i] * z[j];
+    z[i] = s / R[i * kMaxK + i];
+  }
+}
+
+__global__ void k_ve_solve(const ProbDev *__restrict__ probs, int nvec, int update_state) {
+  const ProbDev *P = probs + blockIdx.x;
+  if (update_state && P->st->done) return;
+  if (threadIdx.x != 0) return;
+  const int K = nvec - 1;   // columns of U = kappa + 1
+  const int kap = K - 1;
+  double G[kMaxK * kMaxK];
+  double R[kMaxK * kMaxK];
+  // Gram from chunk partials, fixed order
+  for (int i = 0; i < K; ++i)
+    for (int j = i; j < K; ++j) G[i * kMaxK + j] = 0.0;
+  {
+    int q = 0;
+    for (int i = 0; i < K; ++i)
+      for (int j = i; j < K; ++j, ++q) {
+        double s = 0.0;
+        for (int c = 0; c < P->n_chunks; ++c) s += P->gram_part[(size_t)c * kMaxPairs + q];
+        G[i * kMaxK + j] = s;
+      }
+  }
+  for (int i = 0; i < K * kMaxK; ++i) R[i] = 0.0;
+  // Cholesky with rank checks: r_jj^2 <= tol * ||u_j||^2 marks column j dependent
+  int bad = -1;
+  bool last_bad = false;
+  for (int j = 0; j < K; ++j) {
+    double s = G[j * kMaxK + j];
+    for (int i = 0; i < j; ++i) s -= R[i * kMaxK + j] * R[i * kMaxK + j];
+    const double gjj = G[j * kMaxK + j];
+    if (gjj == 0.0 || s <= kRankTol * gjj) {
+      if (j < K - 1) { bad = j; break; }
+      last_bad = true;
+      R[j * kMaxK + j] = 0.0;
+      break;
+    }
+    const double rjj = sqrt(s);
+    R[j * kMaxK + j] = rjj;
+    for (int l = j + 1; l < K; ++l) {
+      double t = G[j * kMaxK + l];
+      for (int i = 0; i < j; ++i) t -= R[i * kMaxK + j] * R[i * kMaxK + l];
+      R[j * kMaxK + l] = t / rjj;
+    }
+  }
+  double gamma[kMaxK];
+  bool ok = (bad < 0);
+  if (ok) {
+    const int method = P->ve_method;
+    bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
+    if (use_mpe) {
+      double c[kMaxK], rhs[kMaxK];
+      for (int i = 0; i < kap; ++i) rhs[i] = -R[i * kMaxK + kap];
+      if (kap > 0) back_sub(R, rhs, c, kap);
+      c[kap] = 1.0;
+      double sc = 0.0, sa = 0.0;
+      for (int i = 0; i <= kap; ++i) { sc += c[i]; sa += fabs(c[i]); }
+      if (fabs(sc) <= kSumTol * sa) ok = false;
+      else for (int i = 0; i <= kap; ++i) gamma[i] = c[i] / sc;
+    } else {
+      double ones[kMaxK], z[kMaxK], d[kMaxK];
+      for (int i = 0; i < K; ++i) ones[i] = 1.0;
+      fwd_sub_t(R, ones, z, K);
+      back_sub(R, z, d, K);
+      double sd = 0.0;
+      for (int i = 0; i < K; ++i) sd += d[i];
+      for (int i = 0; i < K; ++i) gamma[i] = d[i] / sd;
+    }
+  }
+  ProbState *st = P->st;
+  if (update_state) st->ve_steps += 1;
+  if (!ok) {
+    st->ve_status = 1;
+    if (update_state) st->ve_breakdowns += 1;
+    return;
+  }
+  st->ve_status = 0;
+  double acc = 0.0, sabs = 0.0;
+  for (int j = 0; j < K; ++j) {
+    P->gamma[j] = gamma[j];
+    sabs += fabs(gamma[j]);
+    if (j < kap) {
+      acc += gamma[j];
+      P->ve_coef[j] = 1.0 - acc;   // xi_j
+    }
+  }
+  st->sum_abs_gamma = sabs;
+}
+
+__global__ void __launch_bounds__(256)
+k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  if (va.update_state && P->st->done) return;
+  const int K = va.nvec - 1;
+  const int kap = K - 1;
+  const int begin = it.a * kGramChunk;
+  const int end = min(P->N, begin + kGramChunk);
+  const int brk = P->st->ve_status;
+  float xi[kMaxK];
+  for (int j = 0; j < kap; ++j) xi[j] = (float)P->ve_coef[j];
+  const bool explicit_io = va.ptrs[0] != nullptr;
+  const int bf16 = explicit_io ? 0 : P->storage;
+  const int esz = bf16 ? 2 : 4;
+  void *out = va.out_ptr ? (void *)va.out_ptr
+                         : static_cast<char *>(P->ring) + (size_t)va.out_slot * P->slot_stride * esz;
+  const void *xs[kMaxK + 1];
+  for (int i = 0; i <= K; ++i)
+    xs[i] = va.ptrs[i] ? (const void *)va.ptrs[i]
+                       : static_cast<const char *>(P->ring) + (size_t)va.slots[i] * P->slot_stride * esz;
+  for (int p = begin + threadIdx.x; p < end; p += blockDim.x) {
+    float v;
+    if (brk) {
+      v = load_img(xs[K], p, bf16);
+    } else {
+      float prev = load_img(xs[0], p, bf16);
+      const float x0 = prev;
+      float acc = 0.f;
+      for (int j = 0; j < kap; ++j) {
+        const float nx = load_img(xs[j + 1], p, bf16);
+        acc = fmaf(xi[j], nx - prev, acc);
+        prev = nx;
+      }
+      v = x0 + acc;
+    }
+    store_img(out, p, v, bf16);
+  }
+}
+
+// mode 0: ring slot `slot` <- ptrs[prob] (f32);  mode 1: ptrs[prob] <- final slot (f32)
+__global__ void __launch_bounds__(256)
+k_copy_slots(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int mode, int slot,
+             float *const *ptrs) {
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  const int begin = it.a * kGramChunk;
+  const int end = min(P->N, begin + kGramChunk);
+  const int esz = P->storage ? 2 : 4;
+  float *user = ptrs[it.prob];
+  if (mode == 0) {
+    void *dst = static_cast<char *>(P->ring) + (size_t)slot * P->slot_stride * esz;
+    for (int p = begin + threadIdx.x; p < end; p += blockDim.x) store_img(dst, p, user[p], P->storage);
+  } else {
+    const void *src = static_cast<const char *>(P->ring) + (size_t)P->st->final_slot * P->slot_stride * esz;
+    for (int p = begin + threadIdx.x; p < end; p += blockDim.x) user[p] = load_img(src, p, P->storage);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items,
+                        const VeArgs &va, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int K = va.nvec - 1;
+  switch (K) {
+#define RED_GRAM_CASE(k) \
+  case k: k_gram<k><<<n_items, 256, 0, s>>>(d_probs, d_items, va); break;
+    RED_GRAM_CASE(1) RED_GRAM_CASE(2) RED_GRAM_CASE(3) RED_GRAM_CASE(4) RED_GRAM_CASE(5)
+    RED_GRAM_CASE(6) RED_GRAM_CASE(7) RED_GRAM_CASE(8) RED_GRAM_CASE(9) RED_GRAM_CASE(10)
+#undef RED_GRAM_CASE
+    default:
+      k_gram_generic<<<n_items, 256, 0, s>>>(d_probs, d_items, va);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int update_state,
+                            cudaStream_t s) {
+  if (n_probs <= 0) return cudaSuccess;
+  k_ve_solve<<<n_probs, 32, 0, s>>>(d_probs, nvec, update_state);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
+                           const VeArgs &va, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  k_combine<<<n_items, 256, 0, s>>>(d_probs, d_items, va);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n_items, int mode,
+                              int slot, float *const *d_ptrs, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  k_copy_slots<<<n_items, 256, 0, s>>>(d_probs, d_items, mode, slot, d_ptrs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace red

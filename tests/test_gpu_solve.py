@@ -1,0 +1,146 @@
+"""End-to-end parity of full RED solves (Algorithm 3 around Eq. (7)) on the GPU against
+the FP64 oracle, through the C-ABI, on seeded synthetic problems.
+
+Acceptance for FP32 solves: relative L2 <= 1e-3 and |PSNR difference| <= 0.01 dB against
+the oracle's solve from the same float32 inputs. Batches must reproduce single-problem
+solves exactly (fixed work decomposition, no atomics in any reduction)."""
+import numpy as np
+import pytest
+
+from helpers import f32, psnr, rel_l2, to_dev, to_host
+from oracle import fp as ofp
+from oracle import red as ored
+from paper_1805_02158_gb300 import red, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_solve(p, method, kappa, calls, tol=0.0, m=0, cg_iters=20):
+    F = ofp.FPOperator(f32(p.y), p.psf, (p.height, p.width), p.scale, p.sigma, p.alpha,
+                       cg_iters=cg_iters)
+    return ored.solve(F, f32(p.x0), method, m=m, kappa=kappa, max_calls=calls, tol=tol)
+
+
+def gpu_solve(p, method, k, calls, tol=0.0, m=0, storage="f32", cg_iters=20):
+    import torch
+    P = red.Problem(red.config_for(p, ve=method, ve_k=k, ve_m=m, storage=storage,
+                                   cg_iters=cg_iters), to_dev(p.y))
+    out = torch.empty((p.height, p.width), device="cuda")
+    st = P.solve(to_dev(f32(p.x0)), out, calls, tol)
+    return to_host(out), st
+
+
+@pytest.mark.parametrize("method", ["none", "rre", "mpe"])
+def test_deblur_64_solve_matches_oracle(method):
+    p = synth.deblur_small(0)
+    x_ref, st_ref = oracle_solve(p, method, 4, 50)
+    x, st = gpu_solve(p, method, 5, 50)
+    assert st["fp_calls"] == 50
+    if method != "none":
+        assert st["ve_steps"] == 9 and st_ref["ve_steps"] == 9
+    assert rel_l2(x, x_ref) <= 1e-3
+    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+
+
+def test_deblur_nonsquare_radix3_rre_m1():
+    p = synth.make_deblur(7, 48, 72, synth.gaussian_psf(7, 1.6), 2 ** 0.5)
+    x_ref, _ = oracle_solve(p, "rre", 2, 23, m=1)
+    x, st = gpu_solve(p, "rre", 3, 23, m=1)
+    assert st["fp_calls"] == 23
+    assert rel_l2(x, x_ref) <= 1e-3
+    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+
+
+def test_sr_solve_matches_oracle():
+    p = synth.sr_x3(2, 48)
+    x_ref, _ = oracle_solve(p, "rre", 4, 15)
+    x, st = gpu_solve(p, "rre", 5, 15)
+    assert st["fp_calls"] == 15
+    assert rel_l2(x, x_ref) <= 1e-3
+    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+
+
+def test_ve_beats_plain_fp_in_denoiser_calls():
+    """VE reaches plain FP's final PSNR (50 calls) with fewer calls (Sec. IV claim)."""
+    p = synth.deblur_small(1)
+    x_fp, _ = gpu_solve(p, "none", 5, 50)
+    target = psnr(x_fp, p.x_true)
+    for calls in range(5, 50, 5):
+        x, _ = gpu_solve(p, "rre", 5, calls)
+        if psnr(x, p.x_true) >= target:
+            break
+    assert calls < 50
+
+
+def test_tolerance_termination_and_zero_budget():
+    import torch
+    p = synth.deblur_small(2)
+    x, st = gpu_solve(p, "none", 5, 500, tol=2e-3)
+    x_ref, st_ref = oracle_solve(p, "none", 4, 500, tol=2e-3)
+    assert st["converged"] == 1 and st["rel_change"] < 2e-3
+    assert abs(st["fp_calls"] - st_ref["fp_calls"]) <= 1
+    P = red.Problem(red.config_for(p), to_dev(p.y))
+    x0 = to_dev(f32(p.x0))
+    out = torch.zeros_like(x0)
+    st0 = P.solve(x0, out, 0, 0.0)
+    assert st0["fp_calls"] == 0 and torch.equal(out, x0)
+
+
+def test_batch_equals_single_solves():
+    import torch
+    probs = [synth.deblur_small(3), synth.make_deblur(4, 48, 72, synth.gaussian_psf(7, 1.6), 2.0),
+             synth.make_deblur(5, 96, 96, synth.uniform_psf(9), 1.5)]
+    singles = [gpu_solve(p, "rre", 5, 17)[0] for p in probs]
+    Ps = [red.Problem(red.config_for(p, ve="rre", ve_k=5), to_dev(p.y)) for p in probs]
+    B = red.Batch(Ps)
+    x0s = [to_dev(f32(p.x0)) for p in probs]
+    outs = [torch.empty_like(x) for x in x0s]
+    stats = B.solve(x0s, outs, 17, 0.0)
+    for s, o, ref in zip(stats, outs, singles):
+        assert s["fp_calls"] == 17
+        np.testing.assert_array_equal(to_host(o), ref)
+
+
+def test_batch_host_buffers_match_device_path():
+    import torch
+    probs = [synth.deblur_small(6), synth.deblur_small(7)]
+    Ps = [red.Problem(red.config_for(p), to_dev(p.y)) for p in probs]
+    B = red.Batch(Ps)
+    x0s = [to_dev(f32(p.x0)) for p in probs]
+    outs = [torch.empty_like(x) for x in x0s]
+    B.solve(x0s, outs, 12, 0.0)
+    y_h = [torch.from_numpy(p.y32).pin_memory() for p in probs]
+    x0_h = [torch.from_numpy(p.x0_32).pin_memory() for p in probs]
+    out_h = [torch.empty((64, 64), dtype=torch.float32).pin_memory() for _ in probs]
+    B.solve_host(y_h, x0_h, out_h, 12, 0.0)
+    for a, b in zip(outs, out_h):
+        np.testing.assert_array_equal(to_host(a), b.numpy())
+
+
+def test_bf16_storage_error_is_reported():
+    p = synth.sr_x3(1, 48)
+    x_ref, _ = oracle_solve(p, "rre", 4, 10)
+    x, st = gpu_solve(p, "rre", 5, 10, storage="bf16")
+    d_psnr = abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true))
+    max_abs = float(np.abs(x - x_ref).max())
+    print(f"bf16 storage: PSNR error {d_psnr:.4f} dB, max-abs error {max_abs:.4f}")
+    assert d_psnr <= 0.1 and max_abs <= 2.0
+
+
+def test_objective_matches_oracle():
+    import torch
+    from oracle.nlm import nlm
+    p = synth.deblur_small(8)
+    P = red.Problem(red.config_for(p), to_dev(p.y))
+    x = f32(p.y)
+    e = P.objective(to_dev(x))
+    F = ofp.FPOperator(f32(p.y), p.psf, (64, 64), 1, p.sigma, p.alpha)
+    e_ref = ored.objective(x, nlm(x), f32(p.y), F.otf, 1, p.sigma, p.alpha)
+    assert abs(e - e_ref) <= 1e-4 * abs(e_ref)
+    q = synth.sr_x3(3, 48)
+    Q = red.Problem(red.config_for(q), to_dev(q.y))
+    xq = f32(q.x0)
+    eq = Q.objective(to_dev(xq))
+    Fq = ofp.FPOperator(f32(q.y), q.psf, (48, 48), 3, q.sigma, q.alpha)
+    eq_ref = ored.objective(xq, nlm(xq), f32(q.y), Fq.otf, 3, q.sigma, q.alpha)
+    assert abs(eq - eq_ref) <= 1e-4 * abs(eq_ref)
