@@ -448,9 +448,10 @@ red_status red_destroy_problem(red_problem p) {
 red_status red_denoise(red_problem p, const void *x_dev, void *f_dev, void *stream) {
   return guarded([&] {
     CHECK_ARG(p && x_dev && f_dev, "null argument");
-    StepArgs sa{0, 0, x_dev, static_cast<float *>(f_dev), 0};
+    StepArgs sa{0, 0, x_dev, nullptr, 0};
     CUDA_OK(launch_nlm(p->d_pd, p->plan.d_items + p->plan.off_nlm, p->plan.n_nlm,
-                       p->plan.lc.nlm_wy, sa, 0, static_cast<cudaStream_t>(stream)));
+                       p->plan.lc.nlm_wy, sa, 0, static_cast<cudaStream_t>(stream),
+                       static_cast<float *>(f_dev)));
     return RED_OK;
   });
 }
@@ -505,7 +506,7 @@ red_status red_objective(red_problem p, const void *x_dev, double *e_host, void 
     const float *y = reinterpret_cast<const float *>(b + p->L.y);
     double *obj = reinterpret_cast<double *>(b + p->L.obj);
     // f(x) into the problem's f buffer
-    StepArgs sa{0, 0, x, p->pd.f, 0};
+    StepArgs sa{0, 0, x, nullptr, 0};
     CUDA_OK(launch_nlm(p->d_pd, p->plan.d_items + p->plan.off_nlm, p->plan.n_nlm,
                        p->plan.lc.nlm_wy, sa, 0, s));
     const float *hx = nullptr;

@@ -150,7 +150,7 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   {
     float bt = 1e30f;
     LaunchCfg c = best;
-    for (int wy : {1, 2, 4, 8}) {
+    for (int wy : {1, 2, 4}) {
       c.nlm_wy = wy;
       rebuild(c);
       const float t = time_ms(s, reps, [&] {

@@ -104,8 +104,11 @@ struct LaunchCfg {
   int sr_cluster = 8;      // CTAs per super-resolution cluster (one cluster per problem)
 };
 
+// NLM over the items: reads slot sa.src (or sa.src_ptr), writes f_override or each
+// problem's f buffer.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_is_bf16, cudaStream_t s);
+                       StepArgs sa, int src_is_bf16, cudaStream_t s,
+                       float *f_override = nullptr);
 // FFT launches: items carry (prob, first row/col, count). tw_cap = largest transform
 // length in the launch (M for rows, H for columns); buf_cap = largest per-item buffer
 // (rows * M, or cols * (H + 1)) in complex elements.
@@ -129,6 +132,9 @@ cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_it
                            const VeArgs &va, cudaStream_t s);
 cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n_items,
                               int mode, int slot, float *const *d_ptrs, cudaStream_t s);
+cudaError_t launch_convert_to_slot(const ProbDev *d_prob, const float *src, int slot,
+                                   cudaStream_t s);
+cudaError_t launch_fetch_slot(const ProbDev *d_prob, int slot, float *dst, cudaStream_t s);
 cudaError_t launch_sr_rhs(const ProbDev *d_prob, const float *y, cudaStream_t s);
 cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_sr,
                            int cluster, StepArgs sa, cudaStream_t s);

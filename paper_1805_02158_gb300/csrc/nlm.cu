@@ -41,7 +41,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int R>
 __global__ void __launch_bounds__(128, 3)
 k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArgs sa,
-      int src_is_bf16_override) {
+      int src_is_bf16_override, float *f_override) {
   extern __shared__ float tile[];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
@@ -139,11 +139,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
   }
 
   if (lane == 0 || lane == 31) return;  // halo lanes
-  float *dst;
-  if (sa.dst_ptr)
-    dst = sa.dst_ptr;
-  else
-    dst = P->f;
+  float *dst = f_override ? f_override : P->f;
   const float inv_k = 1.0f / k;
   const int c = tc0 - 2 + 2 * lane;
 #pragma unroll
@@ -165,11 +161,12 @@ cudaError_t nlm_prepare(int wy) {
 }
 
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_is_bf16, cudaStream_t s) {
+                       StepArgs sa, int src_is_bf16, cudaStream_t s, float *f_override) {
   if (n_items <= 0) return cudaSuccess;
+  if (wy < 1 || wy > 4) return cudaErrorInvalidValue;   // kernel is bounded at 128 threads
   const size_t smem = (size_t)(kNlmR * wy + 14) * kStride * sizeof(float);
   dim3 block(32, wy);
-  k_nlm<kNlmR><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16);
+  k_nlm<kNlmR><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -1,15 +1,459 @@
-// Serving loop (continuous batching of RED solves). Placeholder until the scheduler lands.
+// Serving loop: continuous batching of RED solves (Algorithm 3 per request) of different
+// sizes and tasks, admitted by device-memory footprint.
+//
+// One scheduler thread owns the GPU work. Each tick it
+//   1. admits waiting requests (FIFO) while a slot is free and the request's device
+//      footprint fits in the budget: it takes an idle problem of the same shape and
+//      physics from the pool (or creates one), uploads y, recomputes the constants,
+//      writes x0 into ring slot 0 and arms the request's termination state;
+//   2. runs one cycle of Algorithm 3 (ve_m + ve_k FP steps and one extrapolation) for
+//      every running request at once, one launch per phase per group of requests that
+//      share (ve, ve_k, ve_m); requests that meet rel_tol or their budget inside the
+//      cycle stop there, on the device;
+//   3. reads the termination states back (one small copy), returns finished results to
+//      host memory and puts their problems back in the pool, freeing the slot.
+// Every running request starts each cycle from ring slot 0, so newly admitted and
+// running requests share the same launches. A request's arithmetic never depends on the
+// other requests in flight (fixed per-problem work decomposition, no cross-problem
+// reductions), so its result is the same alone and in the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
 #include "red.h"
+#include "runtime.h"
+
+using namespace red;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  red_config cfg{};
+  std::vector<float> psf;
+  std::vector<float> y;
+  float *x_out = nullptr;
+  int max_calls = 0;
+  double tol = 0.0;
+  size_t footprint = 0;
+  std::string key;        // shape + physics: problems with the same key are reusable
+  std::string group;      // (ve, ve_k, ve_m): requests that can share launches
+  red_status status = RED_EBUSY;
+  bool finished = false;
+  red_stats stats{};
+  Clock::time_point t_submit, t_admit, t_done;
+  red_problem_s *prob = nullptr;
+};
+
+std::string key_of(const red_config &c, const std::vector<float> &psf) {
+  std::ostringstream o;
+  o << c.task << "|" << c.height << "x" << c.width << "|" << c.scale << "|" << c.psf_h << "x"
+    << c.psf_w << "|" << c.sigma << "|" << c.alpha << "|" << c.nlm_h << "|" << c.ve << "|"
+    << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|";
+  uint64_t h = 1469598103934665603ull;
+  for (float v : psf) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    h = (h ^ u) * 1099511628211ull;
+  }
+  o << h;
+  return o.str();
+}
+
+std::string group_of(const red_config &c) {
+  std::ostringstream o;
+  o << c.ve << "|" << c.ve_k << "|" << c.ve_m;
+  return o.str();
+}
+
+}  // namespace
+
+struct red_server_s {
+  size_t budget = 0;
+  int max_slots = 1;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> waiting;
+  std::map<uint64_t, std::shared_ptr<Request>> all;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread th;
+  // scheduler-thread state
+  cudaStream_t stream = nullptr;
+  size_t used = 0;                                       // bytes of allocated problems
+  std::map<std::string, std::vector<red_problem_s *>> pool;
+  std::map<std::string, size_t> pool_bytes;
+  std::vector<std::shared_ptr<Request>> running;
+  float *d_stage = nullptr;                              // y / x0 staging (largest image)
+  size_t stage_elems = 0;
+  ProbState *h_states = nullptr;
+  ProbState *d_states = nullptr;
+  int states_cap = 0;
+  red::Plan plan;
+  red::ProbDev *d_pds = nullptr;
+  int pds_cap = 0;
+  std::string sticky_error;
+};
+
+namespace {
+
+void finish(red_server_s *S, const std::shared_ptr<Request> &r, red_status st) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->status = st;
+  r->finished = true;
+  r->t_done = Clock::now();
+  r->stats.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  S->cv_done.notify_all();
+}
+
+void ensure_stage(red_server_s *S, size_t elems) {
+  if (elems <= S->stage_elems) return;
+  if (S->d_stage) cudaFree(S->d_stage);
+  S->d_stage = nullptr;
+  CUDA_OK(cudaMalloc(&S->d_stage, elems * 4));
+  S->stage_elems = elems;
+}
+
+// Frees idle pooled problems until `need` more bytes fit (largest first).
+bool make_room(red_server_s *S, size_t need) {
+  while (S->used + need > S->budget) {
+    std::string best;
+    size_t bb = 0;
+    for (auto &kv : S->pool)
+      if (!kv.second.empty() && S->pool_bytes[kv.first] > bb) {
+        bb = S->pool_bytes[kv.first];
+        best = kv.first;
+      }
+    if (best.empty()) return false;
+    red_problem_s *p = S->pool[best].back();
+    S->pool[best].pop_back();
+    S->used -= bb;
+    delete p;
+  }
+  return true;
+}
+
+// Takes an idle problem for r (or creates one), loads y and x0, arms its state.
+void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
+  cudaStream_t s = S->stream;
+  const int H = r->cfg.height, W = r->cfg.width;
+  const int lh = r->cfg.task == RED_SR ? H / r->cfg.scale : H;
+  const int lw = r->cfg.task == RED_SR ? W / r->cfg.scale : W;
+  ensure_stage(S, (size_t)H * W);
+  CUDA_OK(cudaMemcpyAsync(S->d_stage, r->y.data(), (size_t)lh * lw * 4, cudaMemcpyHostToDevice, s));
+  red_problem_s *P = nullptr;
+  auto &vec = S->pool[r->key];
+  if (!vec.empty()) {
+    P = vec.back();
+    vec.pop_back();
+    red_status st = red_set_observation(P, S->d_stage, 0, s);
+    if (st != RED_OK) throw Fail{st, red_last_error()};
+  } else {
+    red_config c = r->cfg;
+    c.psf = r->psf.data();
+    red_problem out = nullptr;
+    red_status st = red_create_problem(&c, S->d_stage, s, &out);
+    if (st != RED_OK) throw Fail{st, red_last_error()};
+    P = out;
+    S->used += r->footprint;
+    S->pool_bytes[r->key] = r->footprint;
+  }
+  r->prob = P;
+  // x0 = y for deblurring; pixel replication of y, edge-extended, for SR
+  std::vector<float> x0;
+  const float *x0p = r->y.data();
+  if (r->cfg.task == RED_SR) {
+    x0.resize((size_t)H * W);
+    const int sc = r->cfg.scale;
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < W; ++j) {
+        const int li = std::min(i / sc, lh - 1), lj = std::min(j / sc, lw - 1);
+        x0[(size_t)i * W + j] = r->y[(size_t)li * lw + lj];
+      }
+    x0p = x0.data();
+  }
+  char *blk = static_cast<char *>(P->block);
+  if (P->pd.storage == 0) {
+    CUDA_OK(cudaMemcpyAsync(blk + P->L.ring, x0p, (size_t)H * W * 4, cudaMemcpyHostToDevice, s));
+  } else {
+    // bf16 history: stage through f32 and convert with the copy kernel
+    CUDA_OK(cudaMemcpyAsync(blk + P->L.tmp, x0p, (size_t)H * W * 4, cudaMemcpyHostToDevice, s));
+    CUDA_OK(launch_convert_to_slot(P->d_pd, reinterpret_cast<float *>(blk + P->L.tmp), 0, s));
+  }
+  ProbState st{};
+  st.max_calls = r->max_calls;
+  st.tol = r->tol;
+  st.done = r->max_calls <= 0 ? 1 : 0;
+  CUDA_OK(cudaMemcpyAsync(blk + P->L.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  // the x0 host vector must outlive the copy
+  CUDA_OK(cudaStreamSynchronize(s));
+  r->t_admit = Clock::now();
+}
+
+// One cycle of Algorithm 3 for the running requests of one group.
+void run_group_cycle(red_server_s *S, const std::vector<red_problem_s *> &members, int ve, int k,
+                     int m) {
+  cudaStream_t s = S->stream;
+  const int n = (int)members.size();
+  std::vector<ProbDev> pds;
+  for (auto *p : members) pds.push_back(p->pd);   // st = the problem's own state
+  LaunchCfg lc;
+  S->plan.build(pds, lc);
+  for (int i = 0; i < n; ++i) pds[i].n_row_items = S->plan.n_row_items[i];
+  if (n > S->pds_cap) {
+    if (S->d_pds) cudaFree(S->d_pds);
+    S->d_pds = nullptr;
+    CUDA_OK(cudaMalloc(&S->d_pds, sizeof(ProbDev) * n));
+    S->pds_cap = n;
+  }
+  CUDA_OK(cudaMemcpyAsync(S->d_pds, pds.data(), sizeof(ProbDev) * n, cudaMemcpyHostToDevice, s));
+  prepare_launch_attrs(S->plan);
+  for (const CycleOp &op : cycle_ops(ve, k, m)) {
+    if (op.kind == 0) {
+      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
+      launch_fp_step(S->d_pds, S->plan, sa, 0, s);
+    } else {
+      VeArgs va{};
+      for (size_t i = 0; i < op.slots.size(); ++i) va.slots[i] = op.slots[i];
+      va.nvec = (int)op.slots.size();
+      va.out_slot = op.out;
+      va.update_state = 1;
+      launch_ve(S->d_pds, n, S->plan, va, s);
+    }
+  }
+  // the host copy of pds is read by the async copy above
+  CUDA_OK(cudaStreamSynchronize(s));
+}
+
+void scheduler(red_server_s *S) {
+  cudaSetDevice(S->device);
+  while (true) {
+    std::vector<std::shared_ptr<Request>> to_admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->running.empty() && S->waiting.empty()) {
+        if (S->stop) break;
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        continue;
+      }
+      if (S->stop) {
+        for (auto &r : S->waiting) {
+          r->status = RED_ETIMEOUT;
+          r->finished = true;
+        }
+        S->waiting.clear();
+        S->cv_done.notify_all();
+      }
+      // FIFO admission by slots and device footprint
+      while (!S->waiting.empty() &&
+             (int)(S->running.size() + to_admit.size()) < S->max_slots) {
+        auto r = S->waiting.front();
+        const bool pooled = !S->pool[r->key].empty();
+        if (!pooled && !make_room(S, r->footprint)) break;
+        S->waiting.pop_front();
+        to_admit.push_back(r);
+      }
+    }
+    for (auto &r : to_admit) {
+      try {
+        admit(S, r);
+        S->running.push_back(r);
+      } catch (const Fail &e) {
+        r->stats = red_stats{};
+        finish(S, r, e.st);
+      }
+    }
+    if (S->running.empty()) continue;
+    try {
+      std::map<std::string, std::vector<red_problem_s *>> groups;
+      std::map<std::string, const red_config *> gcfg;
+      for (auto &r : S->running) {
+        groups[r->group].push_back(r->prob);
+        gcfg[r->group] = &r->cfg;
+      }
+      for (auto &kv : groups) {
+        const red_config *c = gcfg[kv.first];
+        run_group_cycle(S, kv.second, c->ve, c->ve_k, c->ve_m);
+      }
+      // termination states
+      const int n = (int)S->running.size();
+      if (n > S->states_cap) {
+        if (S->h_states) cudaFreeHost(S->h_states);
+        S->h_states = nullptr;
+        CUDA_OK(cudaMallocHost(&S->h_states, sizeof(ProbState) * n));
+        S->states_cap = n;
+      }
+      for (int i = 0; i < n; ++i) {
+        red_problem_s *P = S->running[i]->prob;
+        CUDA_OK(cudaMemcpyAsync(S->h_states + i, static_cast<char *>(P->block) + P->L.state,
+                                sizeof(ProbState), cudaMemcpyDeviceToHost, S->stream));
+      }
+      CUDA_OK(cudaStreamSynchronize(S->stream));
+      std::vector<std::shared_ptr<Request>> still;
+      for (int i = 0; i < n; ++i) {
+        auto &r = S->running[i];
+        const ProbState &st = S->h_states[i];
+        if (!st.done) {
+          still.push_back(r);
+          continue;
+        }
+        red_problem_s *P = r->prob;
+        CUDA_OK(launch_fetch_slot(P->d_pd, st.final_slot,
+                                  reinterpret_cast<float *>(static_cast<char *>(P->block) + P->L.tmp),
+                                  S->stream));
+        CUDA_OK(cudaMemcpyAsync(r->x_out, static_cast<char *>(P->block) + P->L.tmp,
+                                (size_t)P->pd.N * 4, cudaMemcpyDeviceToHost, S->stream));
+        CUDA_OK(cudaStreamSynchronize(S->stream));
+        r->stats.fp_calls = st.calls;
+        r->stats.ve_steps = st.ve_steps;
+        r->stats.ve_breakdowns = st.ve_breakdowns;
+        r->stats.converged = st.converged;
+        r->stats.rel_change = st.rel_change;
+        r->stats.sum_abs_gamma = st.sum_abs_gamma;
+        S->pool[r->key].push_back(P);
+        r->prob = nullptr;
+        finish(S, r, (r->tol > 0.0 && !st.converged) ? RED_ENOT_CONVERGED : RED_OK);
+      }
+      S->running.swap(still);
+    } catch (const Fail &e) {
+      S->sticky_error = e.msg;
+      for (auto &r : S->running) {
+        if (r->prob) {
+          delete r->prob;
+          r->prob = nullptr;
+        }
+        finish(S, r, e.st);
+      }
+      S->running.clear();
+      S->used = 0;
+      for (auto &kv : S->pool)
+        for (auto *p : kv.second) delete p;
+      S->pool.clear();
+    }
+  }
+}
+
+}  // namespace
 
 extern "C" {
-red_status red_server_create(size_t, int, red_server *out) {
-  if (out) *out = nullptr;
-  return RED_EUNSUPPORTED;
+
+red_status red_server_create(size_t hbm_budget_bytes, int max_slots, red_server *out) {
+  return guarded([&] {
+    CHECK_ARG(out != nullptr, "null output");
+    CHECK_ARG(max_slots >= 1 && hbm_budget_bytes > 0, "need max_slots >= 1 and a budget");
+    std::unique_ptr<red_server_s> S(new red_server_s());
+    S->budget = hbm_budget_bytes;
+    S->max_slots = max_slots;
+    CUDA_OK(cudaGetDevice(&S->device));
+    CUDA_OK(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    red_server_s *raw = S.get();
+    S->th = std::thread([raw] { scheduler(raw); });
+    *out = S.release();
+    return RED_OK;
+  });
 }
-red_status red_submit(red_server, const red_config *, const float *, float *, int, double, uint64_t *) {
-  return RED_EUNSUPPORTED;
+
+red_status red_submit(red_server s, const red_config *cfg, const float *y_host, float *x_out_host,
+                      int max_fp_calls, double rel_tol, uint64_t *ticket) {
+  return guarded([&] {
+    CHECK_ARG(s && cfg && y_host && x_out_host && ticket, "null argument");
+    CHECK_ARG(max_fp_calls >= 0, "max_fp_calls must be >= 0");
+    size_t fp = 0;
+    red_status st = red_problem_footprint(cfg, &fp);
+    if (st != RED_OK) return st;
+    if (fp > s->budget) throw Fail{RED_ENOMEM, "request footprint exceeds the server budget"};
+    auto r = std::make_shared<Request>();
+    r->cfg = *cfg;
+    r->psf.assign(cfg->psf, cfg->psf + (size_t)cfg->psf_h * cfg->psf_w);
+    r->cfg.psf = nullptr;
+    const size_t ny = cfg->task == RED_SR
+                          ? (size_t)(cfg->height / cfg->scale) * (cfg->width / cfg->scale)
+                          : (size_t)cfg->height * cfg->width;
+    r->y.assign(y_host, y_host + ny);
+    r->x_out = x_out_host;
+    r->max_calls = max_fp_calls;
+    r->tol = rel_tol;
+    r->footprint = fp;
+    r->key = key_of(r->cfg, r->psf);
+    r->group = group_of(r->cfg);
+    r->t_submit = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      CHECK_ARG(!s->stop, "server is shutting down");
+      r->ticket = s->next_ticket++;
+      s->all[r->ticket] = r;
+      s->waiting.push_back(r);
+    }
+    s->cv_work.notify_one();
+    *ticket = r->ticket;
+    return RED_OK;
+  });
 }
-red_status red_poll(red_server, uint64_t, red_stats *) { return RED_EUNSUPPORTED; }
-red_status red_wait(red_server, uint64_t, int, red_stats *) { return RED_EUNSUPPORTED; }
-red_status red_server_destroy(red_server) { return RED_OK; }
+
+red_status red_poll(red_server s, uint64_t ticket, red_stats *stats) {
+  return guarded([&] {
+    CHECK_ARG(s != nullptr, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    CHECK_ARG(it != s->all.end(), "unknown ticket");
+    if (!it->second->finished) return RED_EBUSY;
+    if (stats) *stats = it->second->stats;
+    return it->second->status;
+  });
 }
+
+red_status red_wait(red_server s, uint64_t ticket, int timeout_ms, red_stats *stats) {
+  return guarded([&] {
+    CHECK_ARG(s != nullptr, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    CHECK_ARG(it != s->all.end(), "unknown ticket");
+    auto r = it->second;
+    auto pred = [&] { return r->finished; };
+    if (timeout_ms < 0) {
+      s->cv_done.wait(lk, pred);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
+      return RED_ETIMEOUT;
+    }
+    if (stats) *stats = r->stats;
+    return r->status;
+  });
+}
+
+red_status red_server_destroy(red_server s) {
+  return guarded([&] {
+    if (!s) return RED_OK;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->th.joinable()) s->th.join();
+    for (auto &kv : s->pool)
+      for (auto *p : kv.second) delete p;
+    s->plan.release();
+    if (s->d_pds) cudaFree(s->d_pds);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->h_states) cudaFreeHost(s->h_states);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return RED_OK;
+  });
+}
+
+}  // extern "C"

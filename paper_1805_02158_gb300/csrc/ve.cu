@@ -350,7 +350,31 @@ k_copy_slots(const ProbDev *__restrict__ probs, const Item *__restrict__ items, 
   }
 }
 
+// One problem's ring slot <-> a float32 image (storage conversion included).
+__global__ void k_slot_io(const ProbDev *__restrict__ P, int slot, float *img, int to_slot) {
+  const int esz = P->storage ? 2 : 4;
+  char *ring = static_cast<char *>(P->ring) + (size_t)slot * P->slot_stride * esz;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P->N; e += (long)gridDim.x * blockDim.x) {
+    if (to_slot)
+      store_img(ring, e, img[e], P->storage);
+    else
+      img[e] = load_img(ring, e, P->storage);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_convert_to_slot(const ProbDev *d_prob, const float *src, int slot, cudaStream_t s) {
+  k_slot_io<<<152, 256, 0, s>>>(d_prob, slot, const_cast<float *>(src), 1);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fetch_slot(const ProbDev *d_prob, int slot, float *dst, cudaStream_t s) {
+  k_slot_io<<<152, 256, 0, s>>>(d_prob, slot, dst, 0);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items,
                         const VeArgs &va, cudaStream_t s) {

@@ -34,12 +34,13 @@ def deblur_problem(side_h, side_w, seed=0, psf=None):
 
 
 NLM_SIZES = [(8, 8), (48, 72), (64, 64), (96, 128), (144, 192)]
+NLM_PSF = {(8, 8): synth.uniform_psf(3)}
 
 
 @pytest.mark.parametrize("shape", NLM_SIZES)
 def test_nlm_matches_oracle(shape):
     torch = torch_cuda()
-    p = deblur_problem(*shape)
+    p = deblur_problem(*shape, psf=NLM_PSF.get(shape))
     P = red.Problem(red.config_for(p), to_dev(p.y))
     x = f32(p.y)
     f = torch.empty(shape, device="cuda")
