@@ -229,7 +229,7 @@ def main():
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
-    step_ms, nlm_ms, fft_ms, gram_ms, comb_ms = [], [], [], [], []
+    step_ms = []
     l0 = red.kernel_launches()
     if dist:
         dist.barrier()
@@ -247,10 +247,6 @@ def main():
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        nlm_ms.append(B.phase_ms(red.PHASE_NLM)[0])
-        fft_ms.append(B.phase_ms(red.PHASE_FFT)[0])
-        gram_ms.append(B.phase_ms(red.PHASE_GRAM)[0])
-        comb_ms.append(B.phase_ms(red.PHASE_COMBINE)[0])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -261,6 +257,38 @@ def main():
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
+
+    # per-kernel device times: the same K steps with CUDA events recorded around every
+    # phase on the solve's stream (inside the cycle graph when the driver supports timing
+    # graph-recorded events, else with the cycle launched directly)
+    timing_mode = "graph"
+    B.set_phase_timing(True)
+    nlm_ms, fft_ms, gram_ms, comb_ms, pstep_ms = [], [], [], [], []
+    for attempt in range(2):
+        try:
+            B.solve(x0s, outs, CALLS, 0.0)
+            B.phase_ms(red.PHASE_NLM)
+            break
+        except red.RedError:
+            os.environ["RED_NO_GRAPHS"] = "1"
+            timing_mode = "direct launches"
+            B.set_phase_timing(False)
+            B.set_phase_timing(True)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.solve(x0s, outs, CALLS, 0.0)
+        e1.record(stream)
+        e1.synchronize()
+        pstep_ms.append(e0.elapsed_time(e1))
+        nlm_ms.append(B.phase_ms(red.PHASE_NLM)[0])
+        fft_ms.append(B.phase_ms(red.PHASE_FFT)[0])
+        gram_ms.append(B.phase_ms(red.PHASE_GRAM)[0])
+        comb_ms.append(B.phase_ms(red.PHASE_COMBINE)[0])
+    B.set_phase_timing(False)
+    os.environ.pop("RED_NO_GRAPHS", None)
 
     pix = SIDE * SIDE * N_IMAGES
     units = pix * CALLS * args.steps * world
@@ -338,7 +366,8 @@ def main():
                      "peak": nlm_peak, "unit": "Top/s (FP32 lane-ops)",
                      "frac": nlm_achieved / nlm_peak, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_src} max clock)",
-                     "launch_ms": nlm_avg},
+                     "launch_ms": nlm_avg, "timing": f"CUDA events around each launch, {timing_mode}",
+                     "step_ms_with_phase_events": float(np.mean(pstep_ms))},
         "kernels": kern,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -455,10 +455,7 @@ red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launc
     for (auto &e : b->phase_events) {
       if (e.phase != phase) continue;
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
+      CUDA_OK(cudaEventElapsedTime(&ms, e.a, e.b));
       sum += ms;
       ++cnt;
     }
