@@ -53,7 +53,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,7 +70,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -188,10 +188,13 @@ def ve_vs_fp_study(problems, Ps, torch, red):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-study", action="store_true", help="skip the VE-vs-FP call study")
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer (0: none)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -222,7 +225,8 @@ def main():
     B.set_phase_timing(True)
     x0s = [y.clone() for y in ys]
     outs = [torch.empty_like(y) for y in ys]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(max(1, args.flush_mb) * 1024 * 1024 // 4, dtype=torch.float32,
+                        device="cuda")
 
     for _ in range(args.warmup):
         B.solve(x0s, outs, CALLS, 0.0)
@@ -261,19 +265,10 @@ def main():
     # per-kernel device times: the same K steps with CUDA events recorded around every
     # phase on the solve's stream (inside the cycle graph when the driver supports timing
     # graph-recorded events, else with the cycle launched directly)
-    timing_mode = "graph"
+    timing_mode = "direct launches (phase-timed pass)"
     B.set_phase_timing(True)
     nlm_ms, fft_ms, gram_ms, comb_ms, pstep_ms = [], [], [], [], []
-    for attempt in range(2):
-        try:
-            B.solve(x0s, outs, CALLS, 0.0)
-            B.phase_ms(red.PHASE_NLM)
-            break
-        except red.RedError:
-            os.environ["RED_NO_GRAPHS"] = "1"
-            timing_mode = "direct launches"
-            B.set_phase_timing(False)
-            B.set_phase_timing(True)
+    B.solve(x0s, outs, CALLS, 0.0)
     for i in range(args.steps):
         flush.fill_(float(i))
         e0 = torch.cuda.Event(enable_timing=True)
@@ -288,7 +283,6 @@ def main():
         gram_ms.append(B.phase_ms(red.PHASE_GRAM)[0])
         comb_ms.append(B.phase_ms(red.PHASE_COMBINE)[0])
     B.set_phase_timing(False)
-    os.environ.pop("RED_NO_GRAPHS", None)
 
     pix = SIDE * SIDE * N_IMAGES
     units = pix * CALLS * args.steps * world
@@ -296,26 +290,29 @@ def main():
     solves_per_s = N_IMAGES * world * args.steps / (total_ms / 1e3)
 
     # end to end through host buffers (pinned), copies inside the timed region
-    y_h = [torch.from_numpy(p.y.astype(np.float32)).pin_memory() for p in problems]
-    x0_h = [y.clone().pin_memory() for y in y_h]
-    out_h = [torch.empty_like(y).pin_memory() for y in y_h]
-    B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
-    torch.cuda.synchronize()
-    e2e_ms = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e = None
+    if not args.no_e2e:
+        y_h = [torch.from_numpy(p.y.astype(np.float32)).pin_memory() for p in problems]
+        x0_h = [y.clone().pin_memory() for y in y_h]
+        out_h = [torch.empty_like(y).pin_memory() for y in y_h]
         B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = float(sum(e2e_ms))
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = units / (e2e_total / 1e3) / 1e6
-    h2d = sum(int(y.numel()) * 4 for y in y_h) + sum(int(x.numel()) * 4 for x in x0_h)
-    d2h = sum(int(o.numel()) * 4 for o in out_h)
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_total = float(sum(e2e_ms))
+        if dist:
+            t = torch.tensor([e2e_total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        h2d = sum(int(y.numel()) * 4 for y in y_h) + sum(int(x.numel()) * 4 for x in x0_h)
+        d2h = sum(int(o.numel()) * 4 for o in out_h)
+        e2e = {"value": units / (e2e_total / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     pk, pk_src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
@@ -353,7 +350,7 @@ def main():
         if dist:
             dist.barrier()
         return
-    cpu = cpu_oracle_sample()
+    cpu = None if args.no_cpu else cpu_oracle_sample()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -370,7 +367,7 @@ def main():
                      "step_ms_with_phase_events": float(np.mean(pstep_ms))},
         "kernels": kern,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ve_vs_fp": study,

@@ -181,10 +181,11 @@ typedef enum {
   RED_PHASE_COMBINE = 5   /* x_(m,kappa) from gamma                                      */
 } red_phase;
 
-/* Diagnostics. With timing enabled, every cycle records CUDA events around each kernel
- * phase (also inside the captured cycle graph); red_batch_phase_ms then reports the mean
- * device time of one launch of `phase` over the most recent cycle (and how many launches
- * that mean covers). Enabling re-captures the cycle; call between solves. */
+/* Diagnostics. With timing enabled, solves launch their cycles directly (not as a graph)
+ * and record CUDA events around every kernel phase; red_batch_phase_ms then reports the
+ * mean device time of one launch of `phase` over the most recent solve (and how many
+ * launches that mean covers; launches of problems that had already terminated are
+ * included). Call between solves. */
 red_status red_batch_set_phase_timing(red_batch b, int enable);
 red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launches);
 

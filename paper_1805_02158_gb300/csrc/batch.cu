@@ -206,12 +206,13 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   return best;
 }
 
-// Phase timing: events are created once per (cycle op, phase) and recorded around the
-// phase's launches, so a graph replay re-records them.
+// Phase timing: events are created once per (cycle, op, phase) of a solve and recorded
+// around the phase's launches; with timing on, cycles are launched directly (no graph),
+// so every launch of the solve keeps its own event pair.
 struct PhaseScope {
   red_batch_s *b;
   cudaStream_t s;
-  size_t next = 0;
+  size_t &next;
   void begin(int phase) {
     if (!b->phase_timing) return;
     if (next >= b->phase_events.size()) {
@@ -232,7 +233,7 @@ struct PhaseScope {
 void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
   const int n = (int)b->probs.size();
   const Plan &pl = b->plan;
-  PhaseScope ps{b, s};
+  PhaseScope ps{b, s, b->phase_next};
   for (const CycleOp &op : b->ops) {
     if (op.kind == 0) {
       StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
@@ -290,7 +291,7 @@ void ensure_ready(red_batch_s *b, cudaStream_t s) {
     b->ready = true;
   }
   const char *ng = std::getenv("RED_NO_GRAPHS");
-  if (!b->graph && !(ng && *ng == '1')) {
+  if (!b->graph && !b->phase_timing && !(ng && *ng == '1')) {
     if (!b->cap_stream) CUDA_OK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     const uint64_t before = red_kernel_launches();
     CUDA_OK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -372,6 +373,7 @@ red_status batch_solve_impl(red_batch_s *b, const void *const *x0, int max_calls
   CUDA_OK(cudaMemcpyAsync(b->d_states, b->h_states, sizeof(ProbState) * n, cudaMemcpyHostToDevice, s));
   CUDA_OK(launch_copy_slots(b->d_pds, b->plan.d_items + b->plan.off_chunks, b->plan.n_chunks, 0, 0,
                             b->d_ptrs, s));
+  b->phase_next = 0;
   const int max_cycles = max_calls <= 0 ? 0 : (max_calls + b->fp_per_cycle - 1) / b->fp_per_cycle;
   for (int c = 0; c < max_cycles; ++c) {
     run_cycle(b, s);
@@ -452,7 +454,8 @@ red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launc
     CHECK_ARG(b != nullptr && avg_ms != nullptr, "null argument");
     double sum = 0.0;
     int cnt = 0;
-    for (auto &e : b->phase_events) {
+    for (size_t i = 0; i < b->phase_next && i < b->phase_events.size(); ++i) {
+      const auto &e = b->phase_events[i];
       if (e.phase != phase) continue;
       float ms = 0.f;
       CUDA_OK(cudaEventElapsedTime(&ms, e.a, e.b));

@@ -126,7 +126,8 @@ struct red_batch_s {
   std::string tune_key;
   bool phase_timing = false;
   struct PhaseEv { int phase; cudaEvent_t a, b; };
-  std::vector<PhaseEv> phase_events;     // in cycle order, recorded by every replay
+  std::vector<PhaseEv> phase_events;     // launch order within one solve
+  size_t phase_next = 0;                 // events used by the current / last solve
   ~red_batch_s();
 };
 
