@@ -145,19 +145,60 @@ static int auto_cols(int H) {
   return std::max(1, std::min(16, (budget - H) / (2 * (H + 1))));
 }
 
+// Whether the device runs clusters of `ncta` CTAs with the cluster solve's largest
+// shared-memory footprint (checked once per size).
+static bool cluster_ok(int ncta) {
+  static std::mutex mu;
+  static std::map<int, bool> known;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find(ncta);
+  if (it != known.end()) return it->second;
+  const int smem = 220 * 1024;
+  bool ok = fft_cluster_prepare(smem, ncta) == cudaSuccess && fft_cluster_max_active(ncta, smem) >= 1;
+  cudaGetLastError();
+  known[ncta] = ok;
+  return ok;
+}
+
+// RED_FFT_CLUSTER=<n> forces the cluster size of the fused Fourier solve (0: three passes).
+int fft_cluster_override() {
+  const char *e = std::getenv("RED_FFT_CLUSTER");
+  return (e && *e) ? std::atoi(e) : -1;
+}
+
 void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
   release();
   lc = cfg;
+  if (fft_cluster_override() >= 0) lc.fft_cluster = fft_cluster_override();
+  if (lc.fft_cluster > 0 && !cluster_ok(lc.fft_cluster)) lc.fft_cluster = 0;
   std::vector<Item> nlm, rows, cols, chunks;
-  std::vector<int> sr;
+  std::vector<int> sr, fused;
   row_tw_cap = row_buf_cap = col_tw_cap = col_buf_cap = 0;
+  fused_ncta = lc.fft_cluster;
+  fused_tw_m = fused_tw_h = fused_a = fused_buf = 0;
+  const int smem_limit = 220 * 1024;
   n_row_items.assign(pds.size(), 0);
   const int th = kNlmR * lc.nlm_wy;
   for (int p = 0; p < (int)pds.size(); ++p) {
     const ProbDev &d = pds[p];
     for (int r0 = 0; r0 < d.H; r0 += th)
       for (int c0 = 0; c0 < d.W; c0 += kNlmTW) nlm.push_back({p, r0, c0, 0});
-    if (d.task == kDeblur) {
+    bool to_cluster = false;
+    if (d.task == kDeblur && fused_ncta > 0) {
+      int ac = 0, bc = 0;
+      fft_cluster_caps(d.H, d.W, fused_ncta, &ac, &bc);
+      const int tm = std::max(fused_tw_m, d.M), th = std::max(fused_tw_h, d.H);
+      const int aa = std::max(fused_a, ac), bb = std::max(fused_buf, bc);
+      if (fft_cluster_smem(tm, th, aa, bb) <= smem_limit) {
+        fused_tw_m = tm;
+        fused_tw_h = th;
+        fused_a = aa;
+        fused_buf = bb;
+        fused.push_back(p);
+        to_cluster = true;
+      }
+    }
+    if (d.task == kDeblur && !to_cluster) {
       const int rpi = lc.fft_rows > 0 ? lc.fft_rows : auto_rows(d.M);
       int cnt = 0;
       for (int r0 = 0; r0 < d.H; r0 += rpi, ++cnt) rows.push_back({p, r0, rpi, 0});
@@ -168,7 +209,7 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
       for (int c0 = 0; c0 < d.Wh; c0 += cpi) cols.push_back({p, c0, cpi, 0});
       col_tw_cap = std::max(col_tw_cap, d.H);
       col_buf_cap = std::max(col_buf_cap, std::min(cpi, d.Wh) * (d.H + 1));
-    } else {
+    } else if (d.task == kSR) {
       sr.push_back(p);
     }
     for (int c = 0; c < d.n_chunks; ++c) chunks.push_back({p, c, 0, 0});
@@ -194,10 +235,18 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
     CUDA_OK(cudaMalloc(&d_sr, sizeof(int) * n_sr));
     CUDA_OK(cudaMemcpy(d_sr, sr.data(), sizeof(int) * n_sr, cudaMemcpyHostToDevice));
   }
+  n_fused = (int)fused.size();
+  if (n_fused) {
+    CUDA_OK(cudaMalloc(&d_fused, sizeof(int) * n_fused));
+    CUDA_OK(cudaMemcpy(d_fused, fused.data(), sizeof(int) * n_fused, cudaMemcpyHostToDevice));
+  }
 }
 
 void prepare_launch_attrs(const Plan &pl) {
   CUDA_OK(nlm_prepare(pl.lc.nlm_wy));
+  if (pl.n_fused)
+    CUDA_OK(fft_cluster_prepare(fft_cluster_smem(pl.fused_tw_m, pl.fused_tw_h, pl.fused_a, pl.fused_buf),
+                                pl.fused_ncta));
   if (pl.n_rows) CUDA_OK(fft_prepare(pl.row_tw_cap, pl.row_buf_cap, pl.col_tw_cap, pl.col_buf_cap));
   if (pl.n_sr) CUDA_OK(sr_prepare(pl.lc.sr_cluster));
 }
@@ -205,13 +254,18 @@ void prepare_launch_attrs(const Plan &pl) {
 void Plan::release() {
   if (d_items) cudaFree(d_items);
   if (d_sr) cudaFree(d_sr);
+  if (d_fused) cudaFree(d_fused);
   d_items = nullptr;
   d_sr = nullptr;
+  d_fused = nullptr;
+  n_fused = 0;
 }
 
-// One FP step (Eq. (7)) over every problem of a plan.
-void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_bf16, cudaStream_t s) {
-  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s));
+// The Fourier-domain solve of one FP step for every deblurring problem of a plan.
+void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaStream_t s) {
+  if (pl.n_fused)
+    CUDA_OK(launch_fft_solve_cluster(d_probs, pl.d_fused, pl.n_fused, pl.fused_ncta, pl.fused_tw_m,
+                                     pl.fused_tw_h, pl.fused_a, pl.fused_buf, sa, s));
   if (pl.n_rows) {
     CUDA_OK(launch_fft_r2c(d_probs, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
                            pl.row_buf_cap, nullptr, nullptr, sa.update_state, s));
@@ -220,6 +274,12 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
     CUDA_OK(launch_fft_c2r(d_probs, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
                            pl.row_buf_cap, sa, s));
   }
+}
+
+// One FP step (Eq. (7)) over every problem of a plan.
+void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_bf16, cudaStream_t s) {
+  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s));
+  launch_fft_solve(d_probs, pl, sa, s);
   if (pl.n_sr) CUDA_OK(launch_sr_step(d_probs, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, sa, s));
 }
 
@@ -257,6 +317,7 @@ using namespace red;
 red_problem_s::~red_problem_s() {
   if (own_batch) delete own_batch;
   plan.release();
+  plan3.release();
   if (d_pd) cudaFree(d_pd);
   if (block) cudaFree(block);
   if (h_pinned) cudaFreeHost(h_pinned);
@@ -318,9 +379,13 @@ static void fill_prob_dev(red_problem_s *P) {
 void red::problem_upload_pd(red_problem_s *P) {
   std::vector<ProbDev> one{P->pd};
   P->plan.build(one, P->lc);
-  P->pd.n_row_items = P->plan.n_row_items[0];
+  LaunchCfg three = P->lc;
+  three.fft_cluster = 0;
+  P->plan3.build(one, three);
+  P->pd.n_row_items = P->plan3.n_row_items[0];
   CUDA_OK(cudaMemcpy(P->d_pd, &P->pd, sizeof(ProbDev), cudaMemcpyHostToDevice));
   prepare_launch_attrs(P->plan);
+  prepare_launch_attrs(P->plan3);
 }
 
 // Per-problem constants from y (Eq. (7)): deblurring C, G (the PSF spectrum K once per
@@ -331,7 +396,7 @@ void red::problem_precompute(red_problem_s *P, cudaStream_t s) {
   char *b = static_cast<char *>(P->block);
   float *y = reinterpret_cast<float *>(b + P->L.y);
   if (c.task == RED_DEBLUR) {
-    const Plan &pl = P->plan;
+    const Plan &pl = P->plan3;
     float2 *kh = const_cast<float2 *>(d.Kh);
     if (!P->khat_ready) {
       // circularly centred, zero-padded PSF, then K = FFT2 of it
@@ -511,7 +576,7 @@ red_status red_objective(red_problem p, const void *x_dev, double *e_host, void 
                        p->plan.lc.nlm_wy, sa, 0, s));
     const float *hx = nullptr;
     if (p->cfg.task == RED_DEBLUR) {
-      const Plan &pl = p->plan;
+      const Plan &pl = p->plan3;
       CUDA_OK(launch_fft_r2c(p->d_pd, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
                              pl.row_buf_cap, x, nullptr, 0, s));
       CUDA_OK(launch_fft_cols(p->d_pd, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,

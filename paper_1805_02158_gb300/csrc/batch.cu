@@ -71,7 +71,7 @@ bool tune_lookup(const std::string &key, LaunchCfg &out) {
     std::istringstream ss(line);
     std::string k;
     LaunchCfg c;
-    if (ss >> k >> c.nlm_wy >> c.fft_rows >> c.fft_cols >> c.sr_cluster && k == key) {
+    if (ss >> k >> c.nlm_wy >> c.fft_rows >> c.fft_cols >> c.sr_cluster >> c.fft_cluster && k == key) {
       g_tune_mem[key] = c;
       out = c;
       return true;
@@ -87,7 +87,7 @@ void tune_store(const std::string &key, const LaunchCfg &c) {
   if (!path || !*path) return;
   std::ofstream out(path, std::ios::app);
   out << key << " " << c.nlm_wy << " " << c.fft_rows << " " << c.fft_cols << " " << c.sr_cluster
-      << "\n";
+      << " " << c.fft_cluster << "\n";
 }
 
 std::string tune_key(const red_batch_s *b) {
@@ -103,7 +103,7 @@ std::string tune_key(const red_batch_s *b) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  key << "v1|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  key << "v2|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
   for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
   std::string k = key.str();
   std::replace(k.begin(), k.end(), ' ', '_');
@@ -162,8 +162,32 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   bool has_deblur = false, has_sr = false;
   for (auto *p : b->probs) (p->cfg.task == RED_DEBLUR ? has_deblur : has_sr) = true;
   if (has_deblur) {
+    // fused cluster solve (0 = three passes for every problem)
     float bt = 1e30f;
     LaunchCfg c = best;
+    for (int q : {16, 8, 4, 0}) {
+      c.fft_cluster = q;
+      if (q > 0) {
+        int ac = 0, bc = 0, tm = 0, th = 0, aa = 0, bb = 0;
+        for (auto *p : b->probs)
+          if (p->cfg.task == RED_DEBLUR) {
+            fft_cluster_caps(p->pd.H, p->pd.W, q, &ac, &bc);
+            tm = std::max(tm, p->pd.M); th = std::max(th, p->pd.H);
+            aa = std::max(aa, ac); bb = std::max(bb, bc);
+          }
+        const int smem = std::min(fft_cluster_smem(tm, th, aa, bb), 220 * 1024);
+        if (fft_cluster_prepare(smem, q) != cudaSuccess || fft_cluster_max_active(q, smem) < 1) {
+          cudaGetLastError();
+          continue;
+        }
+      }
+      rebuild(c);
+      const Plan &pl = b->plan;
+      const float t = time_ms(s, reps, [&] { launch_fft_solve(b->d_pds, pl, sa, s); });
+      if (t < bt) { bt = t; best.fft_cluster = q; }
+    }
+    bt = 1e30f;
+    c = best;
     for (int r : {0, 2, 4, 8, 16}) {
       c.fft_rows = r;
       rebuild(c);
@@ -240,14 +264,9 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
       ps.begin(RED_PHASE_NLM);
       CUDA_OK(launch_nlm(b->d_pds, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, 0, s));
       ps.end();
-      if (pl.n_rows) {
+      if (pl.n_rows || pl.n_fused) {
         ps.begin(RED_PHASE_FFT);
-        CUDA_OK(launch_fft_r2c(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
-                               pl.row_buf_cap, nullptr, nullptr, 1, s));
-        CUDA_OK(launch_fft_cols(b->d_pds, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,
-                                pl.col_buf_cap, 1, nullptr, 1, s));
-        CUDA_OK(launch_fft_c2r(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
-                               pl.row_buf_cap, sa, s));
+        launch_fft_solve(b->d_pds, pl, sa, s);
         ps.end();
       }
       if (pl.n_sr) {

@@ -11,7 +11,7 @@ namespace red {
 
 constexpr int kMaxK = 16;                       // largest ve_k (columns of U)
 constexpr int kMaxPairs = kMaxK * (kMaxK + 1) / 2;
-constexpr int kGramChunk = 16384;               // pixels per Gram / combine work unit
+constexpr int kGramChunk = 2048;                // pixels per Gram / combine work unit
 constexpr int kNlmR = 8;                        // output rows per NLM thread
 constexpr int kNlmTW = 60;                      // output columns per NLM warp (64 - 4 halo)
 constexpr double kRankTol = 1e-12;              // rank-loss threshold on r_jj^2 / ||u_j||^2
@@ -102,6 +102,7 @@ struct LaunchCfg {
   int fft_rows = 0;        // rows per row-FFT CTA (0 = auto from the row length)
   int fft_cols = 0;        // columns per column-FFT CTA (0 = auto from the column length)
   int sr_cluster = 8;      // CTAs per super-resolution cluster (one cluster per problem)
+  int fft_cluster = 16;    // CTAs per cluster of the fused Fourier solve (0: three passes)
 };
 
 // NLM over the items: reads slot sa.src (or sa.src_ptr), writes f_override or each
@@ -141,6 +142,14 @@ cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_
 cudaError_t launch_objective(const ProbDev *d_prob, const float *x, const float *hx,
                              const float *y, const float *f, double *out, cudaStream_t s);
 
+// Cluster solve (one cluster per deblurring problem, spectrum in shared memory).
+void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems);
+int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap);
+cudaError_t fft_cluster_prepare(int smem, int ncta);
+int fft_cluster_max_active(int ncta, int smem);
+cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, int n, int ncta,
+                                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap,
+                                     StepArgs sa, cudaStream_t s);
 int fft_smem_rows(int tw_cap, int buf_cap);
 int fft_smem_cols(int tw_cap, int buf_cap);
 

@@ -15,7 +15,13 @@
 // (sizes 2^a 3^b), twiddles from tables computed on the host in double precision.
 // Inverse transforms use IFFT(X) = conj(FFT(conj(X))); the 1/(H W) scale is folded
 // into C and G.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace red {
 
@@ -304,6 +310,164 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   }
 }
 
+// The whole solve of one FP step for one problem in one thread-block cluster, with the
+// half spectrum held in the cluster's shared memory (used when it fits):
+//   rows R2C of the CTA's row band -> A (rows x (W/2+1), local shared memory)
+//   cluster barrier; each CTA gathers its band of spectrum columns from every CTA's A
+//   through distributed shared memory, column FFT, X = C + G F, inverse column FFT
+//   cluster barrier; each CTA scatters its columns back into the owners' A
+//   cluster barrier; rows C2R of the band -> x_{k+1}, statistics, termination test.
+// Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
+// x_{k+1} (4 B); the spectrum never leaves the chip.
+__device__ __forceinline__ int band_lo(int q, int n, int ncta) { return (int)((long)q * n / ncta); }
+__device__ __forceinline__ int band_owner(int h, int n, int ncta) {
+  return (int)(((long)(h + 1) * ncta - 1) / n);
+}
+
+__global__ void __launch_bounds__(256)
+k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ list, StepArgs sa,
+                    int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
+  extern __shared__ float2 sm[];
+  __shared__ float part_d, part_x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = cl.block_rank();
+  const int ncta = cl.num_blocks();
+  const ProbDev *P = probs + list[blockIdx.x / ncta];
+  if (sa.update_state && P->st->done) return;   // uniform over the cluster
+  const int H = P->H, W = P->W, M = P->M, Wh = P->Wh;
+  const int r0 = band_lo(rank, H, ncta), nr = band_lo(rank + 1, H, ncta) - r0;
+  const int c0 = band_lo(rank, Wh, ncta), nc = band_lo(rank + 1, Wh, ncta) - c0;
+  const int hs = H + 1;
+  float2 *twm = sm;
+  float2 *tww = twm + tw_cap_m;
+  float2 *twh = tww + tw_cap_m + 1;
+  float2 *A = twh + tw_cap_h;
+  float2 *X0 = A + a_cap;
+  float2 *X1 = X0 + buf_cap;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
+  for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
+  for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
+  // 1. rows of f, real to half spectrum
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    const int row = idx / M, n = idx - row * M;
+    X0[row * M + n] = reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
+  }
+  __syncthreads();
+  const float2 *Z = stockham(X0, X1, M, nr, M, twm, tid, nthr);
+  for (int idx = tid; idx < nr * Wh; idx += nthr) {
+    const int row = idx / Wh, kk = idx - row * Wh;
+    const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
+    const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
+    const float2 t = cmul(tww[kk], csub(zk, zc));
+    const float2 s = cadd(zk, zc);
+    A[row * Wh + kk] = make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
+  }
+  cl.sync();
+  // 2. gather this CTA's spectrum columns from every row band
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    const int h = idx / nc, c = idx - h * nc;
+    const int q = band_owner(h, H, ncta);
+    const float2 *Aq = cl.map_shared_rank(A, q);
+    X0[c * hs + h] = Aq[(h - band_lo(q, H, ncta)) * Wh + c0 + c];
+  }
+  __syncthreads();
+  float2 *F = stockham(X0, X1, H, nc, hs, twh, tid, nthr);
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    const int r = idx / nc, c = idx - r * nc;
+    const long g = (long)r * Wh + c0 + c;
+    const float2 cc = P->Cc[g];
+    const float gg = P->Gg[g];
+    const float2 fv = F[c * hs + r];
+    F[c * hs + r] = make_float2(fmaf(gg, fv.x, cc.x), -fmaf(gg, fv.y, cc.y));  // conj(C + G F)
+  }
+  __syncthreads();
+  const float2 *Xs = stockham(F, F == X0 ? X1 : X0, H, nc, hs, twh, tid, nthr);
+  cl.sync();   // every CTA has finished reading the A bands
+  // 3. scatter the solved columns back to the row bands
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    const int h = idx / nc, c = idx - h * nc;
+    const int q = band_owner(h, H, ncta);
+    float2 *Aq = cl.map_shared_rank(A, q);
+    Aq[(h - band_lo(q, H, ncta)) * Wh + c0 + c] = cconj(Xs[c * hs + h]);
+  }
+  cl.sync();
+  // 4. rows, half spectrum to real, statistics against x_k
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    const int row = idx / M, kk = idx - row * M;
+    const float2 xk = A[row * Wh + kk];
+    const float2 xc = cconj(A[row * Wh + (M - kk)]);
+    const float2 e = cadd(xk, xc);
+    const float2 o = cmul(csub(xk, xc), cconj(tww[kk]));
+    X0[row * M + kk] = cconj(cadd(e, mul_pi(o)));
+  }
+  __syncthreads();
+  const float2 *Y = stockham(X0, X1, M, nr, M, twm, tid, nthr);
+  const int esz = P->storage ? 2 : 4;
+  void *dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
+  const void *src_ring = sa.src_ptr ? sa.src_ptr
+                                    : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
+  const int src_bf16 = sa.src_ptr ? 0 : P->storage;
+  float sd = 0.f, sx = 0.f;
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    const int row = idx / M, n = idx - row * M;
+    const long base = (long)(r0 + row) * W + 2 * n;
+    const float2 v = Y[row * M + n];
+    const float xe = v.x, xo = -v.y;
+    float ye = xe, yo = xo;
+    if (sa.dst_ptr) {
+      reinterpret_cast<float2 *>(sa.dst_ptr + (long)(r0 + row) * W)[n] = make_float2(xe, xo);
+    } else {
+      store_img(dst_ring, base, xe, P->storage);
+      store_img(dst_ring, base + 1, xo, P->storage);
+      if (P->storage) {
+        ye = __bfloat162float(__float2bfloat16_rn(xe));
+        yo = __bfloat162float(__float2bfloat16_rn(xo));
+      }
+    }
+    const float pe = load_img(src_ring, base, src_bf16);
+    const float po = load_img(src_ring, base + 1, src_bf16);
+    sd = fmaf(ye - pe, ye - pe, sd);
+    sd = fmaf(yo - po, yo - po, sd);
+    sx = fmaf(pe, pe, sx);
+    sx = fmaf(po, po, sx);
+  }
+  // CTA sums (fixed order), then rank 0 sums the cluster's partials in rank order
+  __shared__ float red_d[8], red_x[8];
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sd += __shfl_xor_sync(0xffffffffu, sd, off);
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+  }
+  if (lane == 0) { red_d[warp] = sd; red_x[warp] = sx; }
+  __syncthreads();
+  if (tid == 0) {
+    float td = 0.f, tx = 0.f;
+    for (int w = 0; w < (nthr >> 5); ++w) { td += red_d[w]; tx += red_x[w]; }
+    part_d = td;
+    part_x = tx;
+  }
+  cl.sync();
+  if (sa.update_state && rank == 0 && tid == 0) {
+    double tsd = 0.0, tsx = 0.0;
+    for (int q = 0; q < ncta; ++q) {
+      tsd += (double)*cl.map_shared_rank(&part_d, q);
+      tsx += (double)*cl.map_shared_rank(&part_x, q);
+    }
+    ProbState *st = P->st;
+    const double rel = tsx > 0.0 ? sqrt(tsd / tsx) : (tsd > 0.0 ? INFINITY : 0.0);
+    st->rel_change = rel;
+    st->calls += 1;
+    if (rel < st->tol || st->calls >= st->max_calls) {
+      st->done = 1;
+      st->converged = rel < st->tol ? 1 : 0;
+      st->final_slot = sa.dst;
+    }
+  }
+  cl.sync();   // keep shared memory alive until rank 0 has read the partials
+}
+
 __global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,
                                      float2 *Cc, float *Gg, int n, double inv_sigma2,
                                      double alpha, double inv_hw) {
@@ -376,6 +540,72 @@ cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_it
   k_fft_c2r<<<n_items, 256, smem, s>>>(d_probs, d_items, tw_cap, buf_cap, sa);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Shared memory of the cluster solve for one problem (complex elements): twiddles, the
+// row band's half spectrum A, two work buffers (row band rows or column band columns).
+void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems) {
+  const int M = W / 2, Wh = M + 1;
+  const int nr = (H + ncta - 1) / ncta, nc = (Wh + ncta - 1) / ncta;
+  *a_elems = nr * Wh;
+  *buf_elems = std::max(nr * M, nc * (H + 1));
+}
+
+int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
+  return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 2 * (size_t)buf_cap) * sizeof(float2));
+}
+
+static int hw_cluster = 0;
+
+cudaError_t fft_cluster_prepare(int smem, int ncta) {
+  cudaError_t e = set_smem((const void *)k_fft_solve_cluster, smem, &hw_cluster);
+  if (e == cudaSuccess && ncta > 8)
+    e = cudaFuncSetAttribute((const void *)k_fft_solve_cluster,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, int n, int ncta,
+                                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap,
+                                     StepArgs sa, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n * ncta);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = fft_cluster_smem(tw_cap_m, tw_cap_h, a_cap, buf_cap);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ncta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_fft_solve_cluster, d_probs, d_list, sa, tw_cap_m,
+                                     tw_cap_h, a_cap, buf_cap);
+  count_launches(1);
+  return e;
+}
+
+// Largest cluster the device accepts for the cluster solve with this shared memory.
+int fft_cluster_max_active(int ncta, int smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ncta);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ncta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_fft_solve_cluster, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 cudaError_t launch_spectral_constants(const ProbDev *, const float2 *k_hat, const float2 *y_hat,

@@ -61,6 +61,8 @@ struct Plan {
   LaunchCfg lc;
   Item *d_items = nullptr;
   int *d_sr = nullptr;
+  int *d_fused = nullptr;     // deblurring problems solved by the cluster kernel
+  int n_fused = 0, fused_ncta = 0, fused_tw_m = 0, fused_tw_h = 0, fused_a = 0, fused_buf = 0;
   int n_nlm = 0, n_rows = 0, n_cols = 0, n_chunks = 0, n_sr = 0;
   int off_nlm = 0, off_rows = 0, off_cols = 0, off_chunks = 0;
   int row_tw_cap = 0, row_buf_cap = 0, col_tw_cap = 0, col_buf_cap = 0;
@@ -83,6 +85,7 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
                     cudaStream_t s);
 void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs &va,
                cudaStream_t s);
+void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaStream_t s);
 std::vector<CycleOp> cycle_ops(int ve, int k, int m);
 void prepare_launch_attrs(const Plan &pl);
 
@@ -97,7 +100,8 @@ struct red_problem_s {
   red::ProbDev pd{};
   void *block = nullptr;
   red::ProbDev *d_pd = nullptr;
-  red::Plan plan;
+  red::Plan plan;                // FP steps of this problem alone
+  red::Plan plan3;               // three-pass Fourier items (set-up, objective)
   red::LaunchCfg lc;
   char *h_pinned = nullptr;     // 4 KB pinned staging
   red_batch_s *own_batch = nullptr;

@@ -3,13 +3,13 @@
 // From the stored iterates x_m .. x_{m+kappa+1} (K = kappa + 1 differences):
 //   1. k_gram:     G = U^T U, U = [x_{m+1} - x_m, ..., x_{m+K} - x_{m+K-1}], formed on the fly.
 //                  HBM-bound tall-skinny reduction: each work unit (problem, chunk of
-//                  16384 pixels) reads the K + 1 vectors once with 16-byte loads. The
+//                  2048 pixels) reads the K + 1 vectors once with 16-byte loads. The
 //                  differences are split exactly (TwoSum: u = s + e), the products are
 //                  exact (TwoProduct with FMA) and accumulated in double-float (hi + lo)
 //                  per thread, then reduced across the CTA in FP64. The result has
 //                  FP64-level accuracy without FP64 arithmetic in the pixel loop (FP64
 //                  throughput on this part is a small fraction of FP32).
-//   2. k_ve_solve: per problem, one thread: sums the chunk partials in a fixed order,
+//   2. k_ve_solve: per problem, one warp: sums the chunk partials in a fixed order,
 //                  Cholesky G = R^T R (R is the R of Algorithm 2's QR up to signs), then
 //                  MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2) or
 //                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), all in FP64, with
@@ -75,10 +75,10 @@ struct GramAcc {
 };
 
 template <int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
   constexpr int NP = K * (K + 1) / 2;
-  __shared__ double red[8][NP];
+  __shared__ double red[4][NP];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
@@ -187,87 +187,99 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
     P->gram_part[(size_t)it.a * kMaxPairs + q] = red[q];
 }
 
-// Upper-triangular solve R x = b (k x k, row-major with stride kMaxK).
-__device__ void back_sub(const double *R, const double *b, double *x, int k) {
-  for (int i = k - 1; i >= 0; --i) {
-    double s = b[i];
-    for (int j = i + 1; j < k; ++j) s -= R[i * kMaxK + j] * x[j];
-    x[i] = s / R[i * kMaxK + i];
-  }
-}
-
-// R^T z = b (forward substitution with the transpose of upper-triangular R).
-__device__ void fwd_sub_t(const double *R, const double *b, double *z, int k) {
-  for (int i = 0; i < k; ++i) {
-    double s = b[i];
-    for (int j = 0; j < i; ++j) s -= R[j * kMaxK + i] * z[j];
-    z[i] = s / R[i * kMaxK + i];
-  }
-}
-
-__global__ void k_ve_solve(const ProbDev *__restrict__ probs, int nvec, int update_state) {
-  const ProbDev *P = probs + blockIdx.x;
-  if (update_state && P->st->done) return;
-  if (threadIdx.x != 0) return;
-  const int K = nvec - 1;   // columns of U = kappa + 1
-  const int kap = K - 1;
-  double G[kMaxK * kMaxK];
-  double R[kMaxK * kMaxK];
-  // Gram from chunk partials, fixed order
+// The tiny FP64 solve for gamma, one warp per problem. Lanes sum the chunk partials of
+// each Gram entry in a fixed order (lane-strided, then a fixed xor tree); lane 0 then
+// factors G = R^T R and solves for gamma with K-sized register arrays.
+template <int K>
+__device__ void ve_solve_k(const ProbDev *P, int update_state) {
+  constexpr int NP = K * (K + 1) / 2;
+  constexpr int kap = K - 1;
+  const int lane = threadIdx.x & 31;
+  double G[K][K];
+#pragma unroll
+  for (int i = 0, q = 0; i < K; ++i)
+#pragma unroll
+    for (int j = i; j < K; ++j, ++q) {
+      double s = 0.0;
+      for (int c = lane; c < P->n_chunks; c += 32) s += P->gram_part[(size_t)c * kMaxPairs + q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      G[i][j] = s;
+    }
+  (void)NP;
+  if (lane != 0) return;
+  double R[K][K];
+#pragma unroll
   for (int i = 0; i < K; ++i)
-    for (int j = i; j < K; ++j) G[i * kMaxK + j] = 0.0;
-  {
-    int q = 0;
-    for (int i = 0; i < K; ++i)
-      for (int j = i; j < K; ++j, ++q) {
-        double s = 0.0;
-        for (int c = 0; c < P->n_chunks; ++c) s += P->gram_part[(size_t)c * kMaxPairs + q];
-        G[i * kMaxK + j] = s;
-      }
-  }
-  for (int i = 0; i < K * kMaxK; ++i) R[i] = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) R[i][j] = 0.0;
   // Cholesky with rank checks: r_jj^2 <= tol * ||u_j||^2 marks column j dependent
-  int bad = -1;
-  bool last_bad = false;
+  bool bad = false, last_bad = false;
+#pragma unroll
   for (int j = 0; j < K; ++j) {
-    double s = G[j * kMaxK + j];
-    for (int i = 0; i < j; ++i) s -= R[i * kMaxK + j] * R[i * kMaxK + j];
-    const double gjj = G[j * kMaxK + j];
+    if (bad || last_bad) continue;
+    double s = G[j][j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) s -= R[i][j] * R[i][j];
+    const double gjj = G[j][j];
     if (gjj == 0.0 || s <= kRankTol * gjj) {
-      if (j < K - 1) { bad = j; break; }
-      last_bad = true;
-      R[j * kMaxK + j] = 0.0;
-      break;
+      if (j < K - 1) bad = true;
+      else last_bad = true;
+      continue;
     }
     const double rjj = sqrt(s);
-    R[j * kMaxK + j] = rjj;
+    R[j][j] = rjj;
+#pragma unroll
     for (int l = j + 1; l < K; ++l) {
-      double t = G[j * kMaxK + l];
-      for (int i = 0; i < j; ++i) t -= R[i * kMaxK + j] * R[i * kMaxK + l];
-      R[j * kMaxK + l] = t / rjj;
+      double t = G[j][l];
+#pragma unroll
+      for (int i = 0; i < j; ++i) t -= R[i][j] * R[i][l];
+      R[j][l] = t / rjj;
     }
   }
-  double gamma[kMaxK];
-  bool ok = (bad < 0);
+  double gamma[K];
+  bool ok = !bad;
   if (ok) {
     const int method = P->ve_method;
-    bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
+    const bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
     if (use_mpe) {
-      double c[kMaxK], rhs[kMaxK];
-      for (int i = 0; i < kap; ++i) rhs[i] = -R[i * kMaxK + kap];
-      if (kap > 0) back_sub(R, rhs, c, kap);
+      // Algorithm 1 step 2: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1
+      double c[K];
       c[kap] = 1.0;
+#pragma unroll
+      for (int i = kap - 1; i >= 0; --i) {
+        double s = -R[i][kap];
+#pragma unroll
+        for (int j = i + 1; j < kap; ++j) s -= R[i][j] * c[j];
+        c[i] = s / R[i][i];
+      }
       double sc = 0.0, sa = 0.0;
+#pragma unroll
       for (int i = 0; i <= kap; ++i) { sc += c[i]; sa += fabs(c[i]); }
       if (fabs(sc) <= kSumTol * sa) ok = false;
-      else for (int i = 0; i <= kap; ++i) gamma[i] = c[i] / sc;
+#pragma unroll
+      for (int i = 0; i <= kap; ++i) gamma[i] = c[i] / sc;
     } else {
-      double ones[kMaxK], z[kMaxK], d[kMaxK];
-      for (int i = 0; i < K; ++i) ones[i] = 1.0;
-      fwd_sub_t(R, ones, z, K);
-      back_sub(R, z, d, K);
+      // RRE: R^T z = 1 (forward), R d = z (backward), gamma = d / sum d
+      double z[K], d[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        double s = 1.0;
+#pragma unroll
+        for (int j = 0; j < i; ++j) s -= R[j][i] * z[j];
+        z[i] = s / R[i][i];
+      }
+#pragma unroll
+      for (int i = K - 1; i >= 0; --i) {
+        double s = z[i];
+#pragma unroll
+        for (int j = i + 1; j < K; ++j) s -= R[i][j] * d[j];
+        d[i] = s / R[i][i];
+      }
       double sd = 0.0;
+#pragma unroll
       for (int i = 0; i < K; ++i) sd += d[i];
+#pragma unroll
       for (int i = 0; i < K; ++i) gamma[i] = d[i] / sd;
     }
   }
@@ -280,6 +292,7 @@ __global__ void k_ve_solve(const ProbDev *__restrict__ probs, int nvec, int upda
   }
   st->ve_status = 0;
   double acc = 0.0, sabs = 0.0;
+#pragma unroll
   for (int j = 0; j < K; ++j) {
     P->gamma[j] = gamma[j];
     sabs += fabs(gamma[j]);
@@ -291,43 +304,84 @@ __global__ void k_ve_solve(const ProbDev *__restrict__ probs, int nvec, int upda
   st->sum_abs_gamma = sabs;
 }
 
-__global__ void __launch_bounds__(256)
+template <int K>
+__global__ void __launch_bounds__(32) k_ve_solve(const ProbDev *__restrict__ probs, int update_state) {
+  const ProbDev *P = probs + blockIdx.x;
+  if (update_state && P->st->done) return;
+  ve_solve_k<K>(P, update_state);
+}
+
+// Algorithm 1 steps 3-4 without Q: x_(m,kappa) = x_m + sum_{j<kappa} xi_j (x_{m+j+1} - x_{m+j}).
+// On breakdown the output is the last iterate x_{m+kappa+1}.
+template <int K>
+__global__ void __launch_bounds__(128)
 k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
+  constexpr int kap = K - 1;
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
-  const int K = va.nvec - 1;
-  const int kap = K - 1;
   const int begin = it.a * kGramChunk;
   const int end = min(P->N, begin + kGramChunk);
   const int brk = P->st->ve_status;
-  float xi[kMaxK];
+  float xi[kap > 0 ? kap : 1];
+#pragma unroll
   for (int j = 0; j < kap; ++j) xi[j] = (float)P->ve_coef[j];
   const bool explicit_io = va.ptrs[0] != nullptr;
   const int bf16 = explicit_io ? 0 : P->storage;
   const int esz = bf16 ? 2 : 4;
   void *out = va.out_ptr ? (void *)va.out_ptr
                          : static_cast<char *>(P->ring) + (size_t)va.out_slot * P->slot_stride * esz;
-  const void *xs[kMaxK + 1];
+  const void *xs[K + 1];
+#pragma unroll
   for (int i = 0; i <= K; ++i)
     xs[i] = va.ptrs[i] ? (const void *)va.ptrs[i]
                        : static_cast<const char *>(P->ring) + (size_t)va.slots[i] * P->slot_stride * esz;
-  for (int p = begin + threadIdx.x; p < end; p += blockDim.x) {
-    float v;
+  bool vec = !bf16 && ((begin & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+#pragma unroll
+  for (int i = 0; i <= K; ++i) vec = vec && ((reinterpret_cast<uintptr_t>(xs[i]) & 15) == 0);
+  int p0 = begin;
+  if (vec) {
+    const int nv = (end - begin) >> 2;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      float4 r;
+      if (brk) {
+        r = reinterpret_cast<const float4 *>(static_cast<const float *>(xs[K]) + begin)[v];
+      } else {
+        float4 x[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          x[i] = __ldcs(reinterpret_cast<const float4 *>(static_cast<const float *>(xs[i]) + begin) + v);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kap; ++j) {
+          acc.x = fmaf(xi[j], x[j + 1].x - x[j].x, acc.x);
+          acc.y = fmaf(xi[j], x[j + 1].y - x[j].y, acc.y);
+          acc.z = fmaf(xi[j], x[j + 1].z - x[j].z, acc.z);
+          acc.w = fmaf(xi[j], x[j + 1].w - x[j].w, acc.w);
+        }
+        r = make_float4(x[0].x + acc.x, x[0].y + acc.y, x[0].z + acc.z, x[0].w + acc.w);
+      }
+      reinterpret_cast<float4 *>(static_cast<float *>(out) + begin)[v] = r;
+    }
+    p0 = begin + (nv << 2);
+  }
+  for (int p = p0 + threadIdx.x; p < end; p += blockDim.x) {
+    float val;
     if (brk) {
-      v = load_img(xs[K], p, bf16);
+      val = load_img(xs[K], p, bf16);
     } else {
       float prev = load_img(xs[0], p, bf16);
       const float x0 = prev;
       float acc = 0.f;
+#pragma unroll
       for (int j = 0; j < kap; ++j) {
         const float nx = load_img(xs[j + 1], p, bf16);
         acc = fmaf(xi[j], nx - prev, acc);
         prev = nx;
       }
-      v = x0 + acc;
+      val = x0 + acc;
     }
-    store_img(out, p, v, bf16);
+    store_img(out, p, val, bf16);
   }
 }
 
@@ -382,7 +436,7 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
   const int K = va.nvec - 1;
   switch (K) {
 #define RED_GRAM_CASE(k) \
-  case k: k_gram<k><<<n_items, 256, 0, s>>>(d_probs, d_items, va); break;
+  case k: k_gram<k><<<n_items, 128, 0, s>>>(d_probs, d_items, va); break;
     RED_GRAM_CASE(1) RED_GRAM_CASE(2) RED_GRAM_CASE(3) RED_GRAM_CASE(4) RED_GRAM_CASE(5)
     RED_GRAM_CASE(6) RED_GRAM_CASE(7) RED_GRAM_CASE(8) RED_GRAM_CASE(9) RED_GRAM_CASE(10)
 #undef RED_GRAM_CASE
@@ -393,10 +447,19 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
   return cudaGetLastError();
 }
 
+#define RED_K_CASES(M) \
+  M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+
 cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int update_state,
                             cudaStream_t s) {
   if (n_probs <= 0) return cudaSuccess;
-  k_ve_solve<<<n_probs, 32, 0, s>>>(d_probs, nvec, update_state);
+  switch (nvec - 1) {
+#define RED_SOLVE_CASE(k) \
+  case k: k_ve_solve<k><<<n_probs, 32, 0, s>>>(d_probs, update_state); break;
+    RED_K_CASES(RED_SOLVE_CASE)
+#undef RED_SOLVE_CASE
+    default: return cudaErrorInvalidValue;
+  }
   count_launches(1);
   return cudaGetLastError();
 }
@@ -404,7 +467,13 @@ cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int u
 cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
                            const VeArgs &va, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  k_combine<<<n_items, 256, 0, s>>>(d_probs, d_items, va);
+  switch (va.nvec - 1) {
+#define RED_COMBINE_CASE(k) \
+  case k: k_combine<k><<<n_items, 128, 0, s>>>(d_probs, d_items, va); break;
+    RED_K_CASES(RED_COMBINE_CASE)
+#undef RED_COMBINE_CASE
+    default: return cudaErrorInvalidValue;
+  }
   count_launches(1);
   return cudaGetLastError();
 }

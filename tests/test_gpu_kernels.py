@@ -102,6 +102,39 @@ def test_deblur_fp_step_matches_oracle(shape, psf):
     assert rel_l2(to_host(out), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("path", ["0", "4", "16"])
+def test_deblur_fp_step_both_fourier_paths(path, monkeypatch):
+    """The three-pass Fourier solve (RED_FFT_CLUSTER=0) and the cluster solve with 4 or 16
+    CTAs give the oracle's FP step; includes a ragged band split (H = 72 over 16 CTAs)."""
+    torch = torch_cuda()
+    monkeypatch.setenv("RED_FFT_CLUSTER", path)
+    for shape, psf in [((72, 96), synth.gaussian_psf(9, 1.6)), ((128, 128), synth.uniform_psf(9))]:
+        p = deblur_problem(*shape, psf=psf, seed=11)
+        P = red.Problem(red.config_for(p), to_dev(p.y))
+        x = f32(p.y)
+        out = torch.empty(shape, device="cuda")
+        P.fp_step(to_dev(x), out)
+        ref = ofp.deblur_fp_step(x, f32(p.y), oops.psf_otf(p.psf, shape), p.sigma, p.alpha)
+        assert rel_l2(to_host(out), ref) <= 1e-5
+
+
+def test_deblur_fp_step_large_uses_three_passes():
+    """1024 x 1024 does not fit the cluster's shared memory: the three-pass path runs.
+    Checked against the oracle's closed-form solve with f taken from the GPU denoiser
+    (the oracle's own NLM is checked separately at this size by sampling)."""
+    torch = torch_cuda()
+    shape = (1024, 1024)
+    p = deblur_problem(*shape, psf=synth.gaussian_psf(25, 1.6), seed=12)
+    P = red.Problem(red.config_for(p), to_dev(p.y))
+    x = to_dev(f32(p.y))
+    f = torch.empty(shape, device="cuda")
+    P.denoise(x, f)
+    out = torch.empty(shape, device="cuda")
+    P.fp_step(x, out)
+    ref = ofp.deblur_solve(to_host(f), f32(p.y), oops.psf_otf(p.psf, shape), p.sigma, p.alpha)
+    assert rel_l2(to_host(out), ref) <= 1e-5
+
+
 def test_deblur_linear_solve_alone_matches_closed_form():
     """x = [H^T H/s^2 + a I]^{-1}(H^T y/s^2 + a f) with f the oracle's own f(x): isolates the
     FFT solve from the denoiser."""

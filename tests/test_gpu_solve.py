@@ -101,6 +101,26 @@ def test_batch_equals_single_solves():
         np.testing.assert_array_equal(to_host(o), ref)
 
 
+@pytest.mark.parametrize("path", ["0", "16"])
+def test_batch_uneven_sizes_matches_oracle(path, monkeypatch):
+    """An uneven batch (three sizes, two PSFs) through both Fourier paths: every problem
+    matches its own oracle solve."""
+    import torch
+    monkeypatch.setenv("RED_FFT_CLUSTER", path)
+    probs = [synth.make_deblur(20, 48, 48, synth.uniform_psf(9), 2.0),
+             synth.make_deblur(21, 64, 96, synth.gaussian_psf(7, 1.4), 1.2),
+             synth.make_deblur(22, 96, 72, synth.uniform_psf(9), 3.0)]
+    Ps = [red.Problem(red.config_for(p, ve="rre", ve_k=5), to_dev(p.y)) for p in probs]
+    B = red.Batch(Ps)
+    x0s = [to_dev(f32(p.x0)) for p in probs]
+    outs = [torch.empty_like(x) for x in x0s]
+    B.solve(x0s, outs, 16, 0.0)
+    for p, o in zip(probs, outs):
+        x_ref, _ = oracle_solve(p, "rre", 4, 16)
+        assert rel_l2(to_host(o), x_ref) <= 1e-3
+        assert abs(psnr(to_host(o), p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+
+
 def test_batch_host_buffers_match_device_path():
     import torch
     probs = [synth.deblur_small(6), synth.deblur_small(7)]
