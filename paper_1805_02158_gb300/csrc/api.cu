@@ -169,7 +169,6 @@ int fft_cluster_override() {
 void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
   release();
   lc = cfg;
-  if (fft_cluster_override() >= 0) lc.fft_cluster = fft_cluster_override();
   if (lc.fft_cluster > 0 && !cluster_ok(lc.fft_cluster)) lc.fft_cluster = 0;
   std::vector<Item> nlm, rows, cols, chunks;
   std::vector<int> sr, fused;
@@ -477,6 +476,7 @@ red_status red_create_problem(const red_config *cfg, const void *y_dev, void *st
     CUDA_OK(cudaMalloc(&P->d_pd, sizeof(ProbDev)));
     CUDA_OK(cudaMallocHost(&P->h_pinned, 4096));
     fill_prob_dev(P.get());
+    if (fft_cluster_override() >= 0) P->lc.fft_cluster = fft_cluster_override();
     problem_upload_pd(P.get());
     char *b = static_cast<char *>(P->block);
     CUDA_OK(cudaMemcpyAsync(b + P->L.psf, P->psf.data(), sizeof(float) * P->psf.size(),

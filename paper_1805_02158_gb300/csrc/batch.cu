@@ -300,6 +300,7 @@ void ensure_ready(red_batch_s *b, cudaStream_t s) {
       c = autotune(b, s);
       tune_store(b->tune_key, c);
     }
+    if (fft_cluster_override() >= 0) c.fft_cluster = fft_cluster_override();
     b->lc = c;
     b->plan.build(b->pds, c);
     upload_pds(b);

@@ -88,6 +88,7 @@ void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs
 void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaStream_t s);
 std::vector<CycleOp> cycle_ops(int ve, int k, int m);
 void prepare_launch_attrs(const Plan &pl);
+int fft_cluster_override();   // RED_FFT_CLUSTER, or -1 when unset
 
 }  // namespace red
 
