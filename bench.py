@@ -359,6 +359,7 @@ def main():
                    "fp_calls_per_solve": CALLS, "ve": "rre", "k": VE_K,
                    "l2": "flushed between timed steps (512 MB write)"},
         "solves_per_s": solves_per_s,
+        "launch_shapes": B.describe(),
         "roofline": {"bound": "alu", "kernel": "k_nlm", "achieved": nlm_achieved,
                      "peak": nlm_peak, "unit": "Top/s (FP32 lane-ops)",
                      "frac": nlm_achieved / nlm_peak, "traffic": traffic,

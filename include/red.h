@@ -189,6 +189,10 @@ typedef enum {
 red_status red_batch_set_phase_timing(red_batch b, int enable);
 red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launches);
 
+/* Writes a one-line JSON description of the batch's launch shapes (as chosen by the
+ * autotuner on the first solve) into buf (NUL-terminated, truncated to len). */
+red_status red_batch_describe(red_batch b, char *buf, size_t len);
+
 /* ----------------------------------------------------------------------------------- */
 /* Serving: a request loop that continuously batches RED solves of different sizes and  */
 /* tasks as they arrive. Requests are admitted while their device footprint fits in     */

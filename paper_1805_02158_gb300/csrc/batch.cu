@@ -488,6 +488,27 @@ red_status red_batch_phase_ms(red_batch b, int phase, double *avg_ms, int *launc
   });
 }
 
+red_status red_batch_describe(red_batch b, char *buf, size_t len) {
+  return guarded([&] {
+    CHECK_ARG(b != nullptr && buf != nullptr && len > 0, "null argument");
+    const Plan &pl = b->plan;
+    const LaunchCfg &c = b->lc;
+    std::ostringstream o;
+    o << "{\"tuned\": " << (b->ready ? "true" : "false") << ", \"nlm_warps_per_cta\": " << c.nlm_wy
+      << ", \"nlm_ctas\": " << pl.n_nlm << ", \"fft_cluster\": " << pl.fused_ncta
+      << ", \"fft_cluster_problems\": " << pl.n_fused << ", \"fft_row_ctas\": " << pl.n_rows
+      << ", \"fft_col_ctas\": " << pl.n_cols << ", \"sr_cluster\": " << c.sr_cluster
+      << ", \"sr_problems\": " << pl.n_sr << ", \"chunk_ctas\": " << pl.n_chunks
+      << ", \"graph\": " << (b->graph ? "true" : "false") << ", \"graph_kernels_per_cycle\": "
+      << b->graph_kernels << "}";
+    const std::string s = o.str();
+    const size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+    return RED_OK;
+  });
+}
+
 red_status red_solve(red_problem p, const void *x0_dev, int max_fp_calls, double rel_tol,
                      void *x_out_dev, red_stats *stats, void *stream) {
   return guarded([&] {

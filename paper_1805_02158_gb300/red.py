@@ -89,6 +89,7 @@ _SIGS = {
     "red_batch_set_phase_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "red_batch_phase_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int)]),
+    "red_batch_describe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "red_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "red_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
@@ -281,6 +282,13 @@ class Batch:
         for d in out:
             d["status"] = st
         return out
+
+    def describe(self):
+        """The launch shapes the autotuner chose (dict)."""
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        _check(lib().red_batch_describe(self.handle, buf, 1024), "red_batch_describe")
+        return json.loads(buf.value.decode())
 
     def set_phase_timing(self, enable=True):
         _check(lib().red_batch_set_phase_timing(self.handle, int(bool(enable))),
