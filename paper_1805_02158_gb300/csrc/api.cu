@@ -277,7 +277,8 @@ void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaS
 
 // One FP step (Eq. (7)) over every problem of a plan.
 void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_bf16, cudaStream_t s) {
-  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s));
+  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s,
+                     nullptr, pl.lc.nlm_occ));
   launch_fft_solve(d_probs, pl, sa, s);
   if (pl.n_sr) CUDA_OK(launch_sr_step(d_probs, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, sa, s));
 }

@@ -71,7 +71,8 @@ bool tune_lookup(const std::string &key, LaunchCfg &out) {
     std::istringstream ss(line);
     std::string k;
     LaunchCfg c;
-    if (ss >> k >> c.nlm_wy >> c.fft_rows >> c.fft_cols >> c.sr_cluster >> c.fft_cluster && k == key) {
+    if (ss >> k >> c.nlm_wy >> c.nlm_occ >> c.fft_rows >> c.fft_cols >> c.sr_cluster >> c.fft_cluster &&
+        k == key) {
       g_tune_mem[key] = c;
       out = c;
       return true;
@@ -86,7 +87,7 @@ void tune_store(const std::string &key, const LaunchCfg &c) {
   const char *path = std::getenv("RED_TUNE_CACHE");
   if (!path || !*path) return;
   std::ofstream out(path, std::ios::app);
-  out << key << " " << c.nlm_wy << " " << c.fft_rows << " " << c.fft_cols << " " << c.sr_cluster
+  out << key << " " << c.nlm_wy << " " << c.nlm_occ << " " << c.fft_rows << " " << c.fft_cols << " " << c.sr_cluster
       << " " << c.fft_cluster << "\n";
 }
 
@@ -103,7 +104,7 @@ std::string tune_key(const red_batch_s *b) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  key << "v2|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  key << "v3|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
   for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
   std::string k = key.str();
   std::replace(k.begin(), k.end(), ' ', '_');
@@ -141,23 +142,26 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   LaunchCfg best;
   const int n = (int)b->probs.size();
   StepArgs sa{0, 1, nullptr, nullptr, 0};
-  const int reps = 3;
+  const int reps = 5;
   auto rebuild = [&](const LaunchCfg &c) {
     b->plan.build(b->pds, c);
     upload_pds(b);
   };
-  // NLM tile height
+  // NLM tile height and register budget
   {
     float bt = 1e30f;
     LaunchCfg c = best;
-    for (int wy : {1, 2, 4}) {
-      c.nlm_wy = wy;
-      rebuild(c);
-      const float t = time_ms(s, reps, [&] {
-        CUDA_OK(launch_nlm(b->d_pds, b->plan.d_items + b->plan.off_nlm, b->plan.n_nlm, wy, sa, 0, s));
-      });
-      if (t < bt) { bt = t; best.nlm_wy = wy; }
-    }
+    for (int occ : {4, 3})
+      for (int wy : {1, 2, 4}) {
+        c.nlm_wy = wy;
+        c.nlm_occ = occ;
+        rebuild(c);
+        const float t = time_ms(s, reps, [&] {
+          CUDA_OK(launch_nlm(b->d_pds, b->plan.d_items + b->plan.off_nlm, b->plan.n_nlm, wy, sa, 0,
+                             s, nullptr, occ));
+        });
+        if (t < bt) { bt = t; best.nlm_wy = wy; best.nlm_occ = occ; }
+      }
   }
   bool has_deblur = false, has_sr = false;
   for (auto *p : b->probs) (p->cfg.task == RED_DEBLUR ? has_deblur : has_sr) = true;
@@ -262,7 +266,8 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
     if (op.kind == 0) {
       StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
       ps.begin(RED_PHASE_NLM);
-      CUDA_OK(launch_nlm(b->d_pds, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, 0, s));
+      CUDA_OK(launch_nlm(b->d_pds, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, 0, s,
+                         nullptr, pl.lc.nlm_occ));
       ps.end();
       if (pl.n_rows || pl.n_fused) {
         ps.begin(RED_PHASE_FFT);
@@ -495,6 +500,7 @@ red_status red_batch_describe(red_batch b, char *buf, size_t len) {
     const LaunchCfg &c = b->lc;
     std::ostringstream o;
     o << "{\"tuned\": " << (b->ready ? "true" : "false") << ", \"nlm_warps_per_cta\": " << c.nlm_wy
+      << ", \"nlm_ctas_per_sm\": " << c.nlm_occ
       << ", \"nlm_ctas\": " << pl.n_nlm << ", \"fft_cluster\": " << pl.fused_ncta
       << ", \"fft_cluster_problems\": " << pl.n_fused << ", \"fft_row_ctas\": " << pl.n_rows
       << ", \"fft_col_ctas\": " << pl.n_cols << ", \"sr_cluster\": " << c.sr_cluster

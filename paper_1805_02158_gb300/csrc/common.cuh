@@ -99,6 +99,7 @@ struct VeArgs {
 // ---- host-side launch helpers (defined in the .cu files) -------------------------------
 struct LaunchCfg {
   int nlm_wy = 4;          // warps per NLM CTA (tile height = 8 * nlm_wy rows)
+  int nlm_occ = 4;         // resident NLM CTAs per SM the register budget allows (3 or 4)
   int fft_rows = 0;        // rows per row-FFT CTA (0 = auto from the row length)
   int fft_cols = 0;        // columns per column-FFT CTA (0 = auto from the column length)
   int sr_cluster = 8;      // CTAs per super-resolution cluster (one cluster per problem)
@@ -109,7 +110,7 @@ struct LaunchCfg {
 // problem's f buffer.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
                        StepArgs sa, int src_is_bf16, cudaStream_t s,
-                       float *f_override = nullptr);
+                       float *f_override = nullptr, int occ = 4);
 // FFT launches: items carry (prob, first row/col, count). tw_cap = largest transform
 // length in the launch (M for rows, H for columns); buf_cap = largest per-item buffer
 // (rows * M, or cols * (H + 1)) in complex elements.

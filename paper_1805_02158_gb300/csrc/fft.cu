@@ -36,6 +36,19 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // * (-i)
 __device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); }  // * (+i)
 
+// Division by a run-time invariant d < 2^16 for numerators t < 2^16: q = hi32(t * m) with
+// m = floor(2^32 / d) + 1 (exact in that range; d = 1 handled separately). Replaces the
+// integer divisions of the index arithmetic, which otherwise dominate the FFT kernels.
+struct FastDiv {
+  uint32_t d, m;
+  __device__ __forceinline__ explicit FastDiv(int dd) : d((uint32_t)dd), m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
+  __device__ __forceinline__ int div(int t) const { return d == 1 ? t : (int)__umulhi((uint32_t)t, m); }
+  __device__ __forceinline__ void divmod(int t, int &q, int &r) const {
+    q = div(t);
+    r = t - q * (int)d;
+  }
+};
+
 // Forward Stockham FFT of `nseq` sequences of length n held in shared memory (sequence s
 // at x + s * ss). Ping-pongs between x and y; returns the buffer holding the result.
 // Pass with radix r after previous passes of product Ns: butterfly j reads elements
@@ -51,19 +64,21 @@ __device__ float2 *stockham(float2 *x, float2 *y, int n, int nseq, int ss,
     const int nb = n / r;
     const int tws = n / (Ns * r);
     const int total = nseq * nb;
+    const FastDiv dnb(nb), dns(Ns);
     for (int t = tid; t < total; t += nthr) {
-      const int s = t / nb;
-      const int j = t - s * nb;
+      int s, j, g, kk;
+      dnb.divmod(t, s, j);
+      dns.divmod(j, g, kk);
       const float2 *src = in + s * ss;
       float2 *dst = out + s * ss;
-      const int kk = j % Ns;
-      const int base = (j - kk) * r + kk;
+      const int base = g * Ns * r + kk;
       if (r == 4) {
         float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb], a3 = src[j + 3 * nb];
         if (kk) {
-          a1 = cmul(a1, tw[kk * tws]);
-          a2 = cmul(a2, tw[2 * kk * tws]);
-          a3 = cmul(a3, tw[3 * kk * tws]);
+          const int ti = kk * tws;
+          a1 = cmul(a1, tw[ti]);
+          a2 = cmul(a2, tw[2 * ti]);
+          a3 = cmul(a3, tw[3 * ti]);
         }
         const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
         const float2 t3 = mul_mi(csub(a1, a3));
@@ -79,8 +94,9 @@ __device__ float2 *stockham(float2 *x, float2 *y, int n, int nseq, int ss,
       } else {
         float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb];
         if (kk) {
-          a1 = cmul(a1, tw[kk * tws]);
-          a2 = cmul(a2, tw[2 * kk * tws]);
+          const int ti = kk * tws;
+          a1 = cmul(a1, tw[ti]);
+          a2 = cmul(a2, tw[2 * ti]);
         }
         // w = e^{-2 pi i / 3}: y1 = a0 - s/2 - i (sqrt3/2) d, y2 = a0 - s/2 + i (sqrt3/2) d
         const float2 s12 = cadd(a1, a2), d12 = csub(a1, a2);
@@ -121,15 +137,19 @@ k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   const float *src = src_override ? src_override : P->f;
+  const FastDiv fd1(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
-    const int row = idx / M, n = idx - row * M;
+    int row, n;
+    fd1.divmod(idx, row, n);
     b0[row * M + n] = reinterpret_cast<const float2 *>(src + (long)(r0 + row) * W)[n];
   }
   __syncthreads();
   const float2 *Z = stockham(b0, b1, M, nr, M, twm, tid, nthr);
   float2 *dst = dst_override ? dst_override : P->spec;
+  const FastDiv fd2(Wh > 0 ? Wh : 1);
   for (int idx = tid; idx < nr * Wh; idx += nthr) {
-    const int row = idx / Wh, kk = idx - row * Wh;
+    int row, kk;
+    fd2.divmod(idx, row, kk);
     const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
     const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
     // X_k = ((Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k})) / 2
@@ -159,22 +179,28 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   float2 *spec = spec_override ? spec_override : P->spec;
+  const FastDiv fd3(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
-    const int r = idx / nc, c = idx - r * nc;
+    int r, c;
+    fd3.divmod(idx, r, c);
     b0[c * hs + r] = spec[(long)r * Wh + c0 + c];
   }
   __syncthreads();
   float2 *F = stockham(b0, b1, H, nc, hs, twh, tid, nthr);
   if (mode == 0) {
+    const FastDiv fd4(nc > 0 ? nc : 1);
     for (int idx = tid; idx < H * nc; idx += nthr) {
-      const int r = idx / nc, c = idx - r * nc;
+      int r, c;
+      fd4.divmod(idx, r, c);
       spec[(long)r * Wh + c0 + c] = F[c * hs + r];
     }
     return;
   }
   if (mode == 1) {
+    const FastDiv fd5(nc > 0 ? nc : 1);
     for (int idx = tid; idx < H * nc; idx += nthr) {
-      const int r = idx / nc, c = idx - r * nc;
+      int r, c;
+      fd5.divmod(idx, r, c);
       const long g = (long)r * Wh + c0 + c;
       const float2 cc = P->Cc[g];
       const float gg = P->Gg[g];
@@ -184,8 +210,10 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   } else {
     // mode 2: H x for the objective: conj(K F / (H W))
     const float inv_hw = 1.0f / ((float)H * (float)P->W);
+    const FastDiv fd6(nc > 0 ? nc : 1);
     for (int idx = tid; idx < H * nc; idx += nthr) {
-      const int r = idx / nc, c = idx - r * nc;
+      int r, c;
+      fd6.divmod(idx, r, c);
       const float2 kk = P->Kh[(long)r * Wh + c0 + c];
       const float2 v = cmul(kk, F[c * hs + r]);
       F[c * hs + r] = make_float2(v.x * inv_hw, -v.y * inv_hw);
@@ -194,8 +222,10 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   __syncthreads();
   float2 *other = (F == b0) ? b1 : b0;
   const float2 *X = stockham(F, other, H, nc, hs, twh, tid, nthr);
+  const FastDiv fd7(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
-    const int r = idx / nc, c = idx - r * nc;
+    int r, c;
+    fd7.divmod(idx, r, c);
     spec[(long)r * Wh + c0 + c] = cconj(X[c * hs + r]);
   }
 }
@@ -221,8 +251,10 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   __syncthreads();
   const float2 *spec = P->spec;
+  const FastDiv fd8(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
-    const int row = idx / M, kk = idx - row * M;
+    int row, kk;
+    fd8.divmod(idx, row, kk);
     const float2 xk = spec[(long)(r0 + row) * Wh + kk];
     const float2 xc = cconj(spec[(long)(r0 + row) * Wh + (M - kk)]);
     // 2 E_k = X_k + conj X_{M-k};  2 O_k = (X_k - conj X_{M-k}) e^{+2 pi i k / W}
@@ -319,12 +351,14 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
 //   cluster barrier; rows C2R of the band -> x_{k+1}, statistics, termination test.
 // Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
 // x_{k+1} (4 B); the spectrum never leaves the chip.
-__device__ __forceinline__ int band_lo(int q, int n, int ncta) { return (int)((long)q * n / ncta); }
-__device__ __forceinline__ int band_owner(int h, int n, int ncta) {
-  return (int)(((long)(h + 1) * ncta - 1) / n);
+__device__ __forceinline__ int band_lo(int q, int n, const FastDiv &by_ncta) { return by_ncta.div(q * n); }
+__device__ __forceinline__ int band_owner(int h, int ncta, const FastDiv &by_n) {
+  return by_n.div((h + 1) * ncta - 1);
 }
 
-__global__ void __launch_bounds__(256)
+constexpr int kClusterThreads = 512;
+
+__global__ void __launch_bounds__(kClusterThreads)
 k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ list, StepArgs sa,
                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
   extern __shared__ float2 sm[];
@@ -335,8 +369,9 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   const ProbDev *P = probs + list[blockIdx.x / ncta];
   if (sa.update_state && P->st->done) return;   // uniform over the cluster
   const int H = P->H, W = P->W, M = P->M, Wh = P->Wh;
-  const int r0 = band_lo(rank, H, ncta), nr = band_lo(rank + 1, H, ncta) - r0;
-  const int c0 = band_lo(rank, Wh, ncta), nc = band_lo(rank + 1, Wh, ncta) - c0;
+  const FastDiv by_ncta(ncta), by_h(H);
+  const int r0 = band_lo(rank, H, by_ncta), nr = band_lo(rank + 1, H, by_ncta) - r0;
+  const int c0 = band_lo(rank, Wh, by_ncta), nc = band_lo(rank + 1, Wh, by_ncta) - c0;
   const int hs = H + 1;
   float2 *twm = sm;
   float2 *tww = twm + tw_cap_m;
@@ -349,14 +384,18 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   // 1. rows of f, real to half spectrum
+  const FastDiv fd9(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
-    const int row = idx / M, n = idx - row * M;
+    int row, n;
+    fd9.divmod(idx, row, n);
     X0[row * M + n] = reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
   }
   __syncthreads();
   const float2 *Z = stockham(X0, X1, M, nr, M, twm, tid, nthr);
+  const FastDiv fd10(Wh > 0 ? Wh : 1);
   for (int idx = tid; idx < nr * Wh; idx += nthr) {
-    const int row = idx / Wh, kk = idx - row * Wh;
+    int row, kk;
+    fd10.divmod(idx, row, kk);
     const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
     const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
     const float2 t = cmul(tww[kk], csub(zk, zc));
@@ -365,16 +404,20 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   }
   cl.sync();
   // 2. gather this CTA's spectrum columns from every row band
+  const FastDiv fd11(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
-    const int h = idx / nc, c = idx - h * nc;
-    const int q = band_owner(h, H, ncta);
+    int h, c;
+    fd11.divmod(idx, h, c);
+    const int q = band_owner(h, ncta, by_h);
     const float2 *Aq = cl.map_shared_rank(A, q);
-    X0[c * hs + h] = Aq[(h - band_lo(q, H, ncta)) * Wh + c0 + c];
+    X0[c * hs + h] = Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c];
   }
   __syncthreads();
   float2 *F = stockham(X0, X1, H, nc, hs, twh, tid, nthr);
+  const FastDiv fd12(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
-    const int r = idx / nc, c = idx - r * nc;
+    int r, c;
+    fd12.divmod(idx, r, c);
     const long g = (long)r * Wh + c0 + c;
     const float2 cc = P->Cc[g];
     const float gg = P->Gg[g];
@@ -385,16 +428,20 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   const float2 *Xs = stockham(F, F == X0 ? X1 : X0, H, nc, hs, twh, tid, nthr);
   cl.sync();   // every CTA has finished reading the A bands
   // 3. scatter the solved columns back to the row bands
+  const FastDiv fd13(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
-    const int h = idx / nc, c = idx - h * nc;
-    const int q = band_owner(h, H, ncta);
+    int h, c;
+    fd13.divmod(idx, h, c);
+    const int q = band_owner(h, ncta, by_h);
     float2 *Aq = cl.map_shared_rank(A, q);
-    Aq[(h - band_lo(q, H, ncta)) * Wh + c0 + c] = cconj(Xs[c * hs + h]);
+    Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c] = cconj(Xs[c * hs + h]);
   }
   cl.sync();
   // 4. rows, half spectrum to real, statistics against x_k
+  const FastDiv fd14(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
-    const int row = idx / M, kk = idx - row * M;
+    int row, kk;
+    fd14.divmod(idx, row, kk);
     const float2 xk = A[row * Wh + kk];
     const float2 xc = cconj(A[row * Wh + (M - kk)]);
     const float2 e = cadd(xk, xc);
@@ -409,8 +456,10 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
                                     : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
   const int src_bf16 = sa.src_ptr ? 0 : P->storage;
   float sd = 0.f, sx = 0.f;
+  const FastDiv fd15(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
-    const int row = idx / M, n = idx - row * M;
+    int row, n;
+    fd15.divmod(idx, row, n);
     const long base = (long)(r0 + row) * W + 2 * n;
     const float2 v = Y[row * M + n];
     const float xe = v.x, xo = -v.y;
@@ -433,7 +482,7 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     sx = fmaf(po, po, sx);
   }
   // CTA sums (fixed order), then rank 0 sums the cluster's partials in rank order
-  __shared__ float red_d[8], red_x[8];
+  __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -571,7 +620,7 @@ cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, 
   if (n <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n * ncta);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kClusterThreads);
   cfg.dynamicSmemBytes = fft_cluster_smem(tw_cap_m, tw_cap_h, a_cap, buf_cap);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -591,7 +640,7 @@ cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, 
 int fft_cluster_max_active(int ncta, int smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ncta);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kClusterThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

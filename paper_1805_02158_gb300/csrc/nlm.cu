@@ -38,8 +38,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-template <int R>
-__global__ void __launch_bounds__(128, 3)
+template <int R, int MINB>
+__global__ void __launch_bounds__(128, MINB)
 k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArgs sa,
       int src_is_bf16_override, float *f_override) {
   extern __shared__ float tile[];
@@ -108,18 +108,19 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
         d0[rr] = a0[rr] - b0[rr + dyi];
         d1[rr] = a1[rr] - b1[rr + dyi];
       }
-      float v0 = d0[0] * d0[0];
-      float v1 = d1[0] * d1[0];
+      // negated 5-row sums of squared differences (so a weight is ex2 of the sum)
+      float v0 = (-d0[0]) * d0[0];
+      float v1 = (-d1[0]) * d1[0];
 #pragma unroll
       for (int t = 1; t < 5; ++t) {
-        v0 = fmaf(d0[t], d0[t], v0);
-        v1 = fmaf(d1[t], d1[t], v1);
+        v0 = fmaf(-d0[t], d0[t], v0);
+        v1 = fmaf(-d1[t], d1[t], v1);
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (r > 0) {
-          v0 = fmaf(d0[r + 4], d0[r + 4], fmaf(-d0[r - 1], d0[r - 1], v0));
-          v1 = fmaf(d1[r + 4], d1[r + 4], fmaf(-d1[r - 1], d1[r - 1], v1));
+          v0 = fmaf(-d0[r + 4], d0[r + 4], fmaf(d0[r - 1], d0[r - 1], v0));
+          v1 = fmaf(-d1[r + 4], d1[r + 4], fmaf(d1[r - 1], d1[r - 1], v1));
         }
         const float p = v0 + v1;
         const float pl = __shfl_up_sync(kFull, p, 1);
@@ -128,8 +129,8 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
         const float v0r = __shfl_down_sync(kFull, v0, 1);
         const float D0 = (pl + p) + v0r;
         const float D1 = (v1l + p) + pr;
-        const float w0 = ex2_approx(-D0);
-        const float w1 = ex2_approx(-D1);
+        const float w0 = ex2_approx(D0);
+        const float w1 = ex2_approx(D1);
         num0[r] = fmaf(w0, b0[r + 2 + dyi], num0[r]);
         num1[r] = fmaf(w1, b1[r + 2 + dyi], num1[r]);
         den0[r] += w0;
@@ -155,18 +156,22 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
 
 cudaError_t nlm_prepare(int wy) {
   const int smem = (kNlmR * wy + 14) * kStride * (int)sizeof(float);
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute((const void *)k_nlm<kNlmR>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  (void)smem;   // at most 4 warps per CTA: always under the 48 KB default
+  return cudaSuccess;
 }
 
+// occ: 3 or 4 resident CTAs per SM (the register budget: 161 or 128 per thread); the
+// arithmetic, and so the result, is the same for both.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_is_bf16, cudaStream_t s, float *f_override) {
+                       StepArgs sa, int src_is_bf16, cudaStream_t s, float *f_override, int occ) {
   if (n_items <= 0) return cudaSuccess;
   if (wy < 1 || wy > 4) return cudaErrorInvalidValue;   // kernel is bounded at 128 threads
   const size_t smem = (size_t)(kNlmR * wy + 14) * kStride * sizeof(float);
   dim3 block(32, wy);
-  k_nlm<kNlmR><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
+  if (occ >= 4)
+    k_nlm<kNlmR, 4><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
+  else
+    k_nlm<kNlmR, 3><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
   count_launches(1);
   return cudaGetLastError();
 }
