@@ -49,6 +49,25 @@ struct FastDiv {
   }
 };
 
+// Copies `total` elements with U independent loads in flight per thread (load all, then
+// store all), instead of one load-to-use round trip per loop iteration.
+template <int U, class Load, class Store>
+__device__ __forceinline__ void copy_batched(int total, int tid, int nthr, Load load, Store store) {
+  for (int base = tid; base < total; base += U * nthr) {
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) v[u] = load(idx);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) store(idx, v[u]);
+    }
+  }
+}
+
 // Forward Stockham FFT of `nseq` sequences of length n held in shared memory (sequence s
 // at x + s * ss). Ping-pongs between x and y; returns the buffer holding the result.
 // Pass with radix r after previous passes of product Ns: butterfly j reads elements
@@ -384,12 +403,14 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   // 1. rows of f, real to half spectrum
-  const FastDiv fd9(M > 0 ? M : 1);
-  for (int idx = tid; idx < nr * M; idx += nthr) {
-    int row, n;
-    fd9.divmod(idx, row, n);
-    X0[row * M + n] = reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
-  }
+  const FastDiv fdm(M);
+  copy_batched<4>(nr * M, tid, nthr,
+      [&](int idx) {
+        int row, n;
+        fdm.divmod(idx, row, n);
+        return reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
+      },
+      [&](int idx, float2 v) { X0[idx] = v; });
   __syncthreads();
   const float2 *Z = stockham(X0, X1, M, nr, M, twm, tid, nthr);
   const FastDiv fd10(Wh > 0 ? Wh : 1);
@@ -404,25 +425,46 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   }
   cl.sync();
   // 2. gather this CTA's spectrum columns from every row band
-  const FastDiv fd11(nc > 0 ? nc : 1);
-  for (int idx = tid; idx < H * nc; idx += nthr) {
-    int h, c;
-    fd11.divmod(idx, h, c);
-    const int q = band_owner(h, ncta, by_h);
-    const float2 *Aq = cl.map_shared_rank(A, q);
-    X0[c * hs + h] = Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c];
-  }
+  const FastDiv fdc(nc > 0 ? nc : 1);
+  copy_batched<8>(H * nc, tid, nthr,
+      [&](int idx) {
+        int h, c;
+        fdc.divmod(idx, h, c);
+        const int q = band_owner(h, ncta, by_h);
+        const float2 *Aq = cl.map_shared_rank(A, q);
+        return Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c];
+      },
+      [&](int idx, float2 v) {
+        int h, c;
+        fdc.divmod(idx, h, c);
+        X0[c * hs + h] = v;
+      });
   __syncthreads();
   float2 *F = stockham(X0, X1, H, nc, hs, twh, tid, nthr);
-  const FastDiv fd12(nc > 0 ? nc : 1);
-  for (int idx = tid; idx < H * nc; idx += nthr) {
-    int r, c;
-    fd12.divmod(idx, r, c);
-    const long g = (long)r * Wh + c0 + c;
-    const float2 cc = P->Cc[g];
-    const float gg = P->Gg[g];
-    const float2 fv = F[c * hs + r];
-    F[c * hs + r] = make_float2(fmaf(gg, fv.x, cc.x), -fmaf(gg, fv.y, cc.y));  // conj(C + G F)
+  for (int base = tid; base < H * nc; base += 4 * nthr) {
+    float2 cc[4];
+    float gg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < H * nc) {
+        int r, c;
+        fdc.divmod(idx, r, c);
+        const long g = (long)r * Wh + c0 + c;
+        cc[u] = P->Cc[g];
+        gg[u] = P->Gg[g];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < H * nc) {
+        int r, c;
+        fdc.divmod(idx, r, c);
+        const float2 fv = F[c * hs + r];
+        F[c * hs + r] = make_float2(fmaf(gg[u], fv.x, cc[u].x), -fmaf(gg[u], fv.y, cc[u].y));  // conj(C + G F)
+      }
+    }
   }
   __syncthreads();
   const float2 *Xs = stockham(F, F == X0 ? X1 : X0, H, nc, hs, twh, tid, nthr);
@@ -456,30 +498,45 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
                                     : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
   const int src_bf16 = sa.src_ptr ? 0 : P->storage;
   float sd = 0.f, sx = 0.f;
-  const FastDiv fd15(M > 0 ? M : 1);
-  for (int idx = tid; idx < nr * M; idx += nthr) {
-    int row, n;
-    fd15.divmod(idx, row, n);
-    const long base = (long)(r0 + row) * W + 2 * n;
-    const float2 v = Y[row * M + n];
-    const float xe = v.x, xo = -v.y;
-    float ye = xe, yo = xo;
-    if (sa.dst_ptr) {
-      reinterpret_cast<float2 *>(sa.dst_ptr + (long)(r0 + row) * W)[n] = make_float2(xe, xo);
-    } else {
-      store_img(dst_ring, base, xe, P->storage);
-      store_img(dst_ring, base + 1, xo, P->storage);
-      if (P->storage) {
-        ye = __bfloat162float(__float2bfloat16_rn(xe));
-        yo = __bfloat162float(__float2bfloat16_rn(xo));
+  // previous iterate x_k for the statistics: 4 pixel pairs in flight per thread
+  for (int b0 = tid; b0 < nr * M; b0 += 4 * nthr) {
+    float2 prev[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = b0 + u * nthr;
+      if (idx < nr * M) {
+        int row, n;
+        fdm.divmod(idx, row, n);
+        const long base = (long)(r0 + row) * W + 2 * n;
+        prev[u] = make_float2(load_img(src_ring, base, src_bf16), load_img(src_ring, base + 1, src_bf16));
       }
     }
-    const float pe = load_img(src_ring, base, src_bf16);
-    const float po = load_img(src_ring, base + 1, src_bf16);
-    sd = fmaf(ye - pe, ye - pe, sd);
-    sd = fmaf(yo - po, yo - po, sd);
-    sx = fmaf(pe, pe, sx);
-    sx = fmaf(po, po, sx);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = b0 + u * nthr;
+      if (idx >= nr * M) break;
+      int row, n;
+      fdm.divmod(idx, row, n);
+      const long base = (long)(r0 + row) * W + 2 * n;
+      const float2 v = Y[row * M + n];
+      const float xe = v.x, xo = -v.y;
+      float ye = xe, yo = xo;
+      if (sa.dst_ptr) {
+        reinterpret_cast<float2 *>(sa.dst_ptr + (long)(r0 + row) * W)[n] = make_float2(xe, xo);
+      } else {
+        store_img(dst_ring, base, xe, P->storage);
+        store_img(dst_ring, base + 1, xo, P->storage);
+        if (P->storage) {
+          ye = __bfloat162float(__float2bfloat16_rn(xe));
+          yo = __bfloat162float(__float2bfloat16_rn(xo));
+        }
+      }
+      const float pe = prev[u].x, po = prev[u].y;
+      sd = fmaf(ye - pe, ye - pe, sd);
+      sd = fmaf(yo - po, yo - po, sd);
+      sx = fmaf(pe, pe, sx);
+      sx = fmaf(po, po, sx);
+    }
   }
   // CTA sums (fixed order), then rank 0 sums the cluster's partials in rank order
   __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];

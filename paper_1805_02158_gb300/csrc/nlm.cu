@@ -32,6 +32,13 @@ constexpr int kCols = kNlmTW + 14;   // staged columns: [tc0 - 7, tc0 + 67)
 constexpr int kStride = 76;          // shared-memory row stride (floats)
 constexpr unsigned kFull = 0xffffffffu;
 
+// Half-sample symmetric reflection for indices within one side length of the image,
+// then clamped into it.
+__device__ __forceinline__ int reflect_clamp(int i, int n) {
+  i = i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+  return min(max(i, 0), n - 1);
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -64,14 +71,33 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
           (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
   }
 
+  // Stage the tile: 8 loads in flight per thread. One reflection is exact for every pixel
+  // an output inside the image needs (halo 7 <= side); the clamp only keeps rows/columns
+  // of partial tiles, whose outputs are not stored, inside the image.
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int nthr = 32 * wy;
-  for (int idx = tid; idx < rows * kCols; idx += nthr) {
-    const int rr = idx / kCols;
-    const int cc = idx - rr * kCols;
-    const int gr = mirror_index(tr0 - 7 + rr, H);
-    const int gc = mirror_index(tc0 - 7 + cc, W);
-    tile[rr * kStride + cc] = k * load_img(src, (long)gr * W + gc, bf16);
+  const int total = rows * kCols;
+  for (int base = tid; base < total; base += 8 * nthr) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) {
+        const int rr = idx / kCols;
+        const int cc = idx - rr * kCols;
+        const int gr = reflect_clamp(tr0 - 7 + rr, H);
+        const int gc = reflect_clamp(tc0 - 7 + cc, W);
+        v[u] = load_img(src, (long)gr * W + gc, bf16);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) {
+        const int rr = idx / kCols;
+        tile[rr * kStride + (idx - rr * kCols)] = k * v[u];
+      }
+    }
   }
   __syncthreads();
 

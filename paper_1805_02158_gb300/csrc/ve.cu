@@ -99,23 +99,44 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
     int p0 = begin;
     if (aligned) {
       const int nv = (end - begin) >> 2;
-      for (int v = tid; v < nv; v += blockDim.x) {
-        float4 q[K + 1];
+      const int step = blockDim.x;
+      constexpr bool kDual = K <= 6;   // two loads per vector in flight where registers allow
+      for (int v = tid; v < nv; v += (kDual ? 2 : 1) * step) {
+        float4 q0[K + 1], q1[K + 1];
+        const bool has1 = kDual && v + step < nv;
 #pragma unroll
-        for (int i = 0; i <= K; ++i) q[i] = __ldcs(reinterpret_cast<const float4 *>(xp[i] + begin) + v);
+        for (int i = 0; i <= K; ++i) {
+          const float4 *src = reinterpret_cast<const float4 *>(xp[i] + begin);
+          q0[i] = __ldcs(src + v);
+          if (has1) q1[i] = __ldcs(src + v + step);
+        }
         float x[K + 1];
 #pragma unroll
-        for (int i = 0; i <= K; ++i) x[i] = q[i].x;
+        for (int i = 0; i <= K; ++i) x[i] = q0[i].x;
         acc.add(x);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) x[i] = q[i].y;
+        for (int i = 0; i <= K; ++i) x[i] = q0[i].y;
         acc.add(x);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) x[i] = q[i].z;
+        for (int i = 0; i <= K; ++i) x[i] = q0[i].z;
         acc.add(x);
 #pragma unroll
-        for (int i = 0; i <= K; ++i) x[i] = q[i].w;
+        for (int i = 0; i <= K; ++i) x[i] = q0[i].w;
         acc.add(x);
+        if (has1) {
+#pragma unroll
+          for (int i = 0; i <= K; ++i) x[i] = q1[i].x;
+          acc.add(x);
+#pragma unroll
+          for (int i = 0; i <= K; ++i) x[i] = q1[i].y;
+          acc.add(x);
+#pragma unroll
+          for (int i = 0; i <= K; ++i) x[i] = q1[i].z;
+          acc.add(x);
+#pragma unroll
+          for (int i = 0; i <= K; ++i) x[i] = q1[i].w;
+          acc.add(x);
+        }
       }
       p0 = begin + (nv << 2);
     }
@@ -136,14 +157,23 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
       acc.add(x);
     }
   }
-  // CTA reduction in FP64, fixed order
+  // warp reduction in double-float (FP32 units, TwoSum), fixed xor order; FP64 only for
+  // the final per-warp value and the sum over the CTA's warps
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    double v = (double)acc.hi[q] + (double)acc.lo[q];
+    float h = acc.hi[q], l = acc.lo[q];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red[warp][q] = v;
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+      const float s = __fadd_rn(h, h2);
+      const float z = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
+      h = s;
+      l = __fadd_rn(__fadd_rn(l, l2), e);
+    }
+    if (lane == 0) red[warp][q] = (double)h + (double)l;
   }
   __syncthreads();
   if (tid < NP) {
