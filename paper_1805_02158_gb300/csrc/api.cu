@@ -142,7 +142,7 @@ static void validate(const red_config *c) {
 static int auto_rows(int M) { return std::max(1, std::min(16, 2048 / M)); }
 static int auto_cols(int H) {
   const int budget = 200 * 1024 / 8;
-  return std::max(1, std::min(16, (budget - H) / (2 * (H + 1))));
+  return std::max(1, std::min(16, (budget - H) / (2 * fft_seq_stride(H))));
 }
 
 // Whether the device runs clusters of `ncta` CTAs with the cluster solve's largest
@@ -177,10 +177,9 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
   fused_tw_m = fused_tw_h = fused_a = fused_buf = 0;
   const int smem_limit = 220 * 1024;
   n_row_items.assign(pds.size(), 0);
-  const int th = kNlmR * lc.nlm_wy;
   for (int p = 0; p < (int)pds.size(); ++p) {
     const ProbDev &d = pds[p];
-    for (int r0 = 0; r0 < d.H; r0 += th)
+    for (int r0 = 0; r0 < d.H; r0 += kNlmR)
       for (int c0 = 0; c0 < d.W; c0 += kNlmTW) nlm.push_back({p, r0, c0, 0});
     bool to_cluster = false;
     if (d.task == kDeblur && fused_ncta > 0) {
@@ -203,11 +202,11 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
       for (int r0 = 0; r0 < d.H; r0 += rpi, ++cnt) rows.push_back({p, r0, rpi, 0});
       n_row_items[p] = cnt;
       row_tw_cap = std::max(row_tw_cap, d.M);
-      row_buf_cap = std::max(row_buf_cap, std::min(rpi, d.H) * d.M);
+      row_buf_cap = std::max(row_buf_cap, std::min(rpi, d.H) * fft_seq_stride(d.M));
       const int cpi = lc.fft_cols > 0 ? std::min(lc.fft_cols, auto_cols(d.H)) : auto_cols(d.H);
       for (int c0 = 0; c0 < d.Wh; c0 += cpi) cols.push_back({p, c0, cpi, 0});
       col_tw_cap = std::max(col_tw_cap, d.H);
-      col_buf_cap = std::max(col_buf_cap, std::min(cpi, d.Wh) * (d.H + 1));
+      col_buf_cap = std::max(col_buf_cap, std::min(cpi, d.Wh) * fft_seq_stride(d.H));
     } else if (d.task == kSR) {
       sr.push_back(p);
     }

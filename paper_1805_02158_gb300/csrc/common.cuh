@@ -160,6 +160,10 @@ cudaError_t sr_prepare(int cluster);
 cudaError_t nlm_prepare(int wy);
 
 // ---- small device helpers ---------------------------------------------------------------
+// Stride of one transform sequence of length n in shared memory: one pad slot per 16
+// elements, rounded up to odd (bank-conflict-free strided and transposed accesses).
+__host__ __device__ __forceinline__ int fft_seq_stride(int n) { return (n + (n >> 4)) | 1; }
+
 __host__ __device__ __forceinline__ int mirror_index(int i, int n) {
   // half-sample symmetric reflection into [0, n), period 2n
   int p = 2 * n;

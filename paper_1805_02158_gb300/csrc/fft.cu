@@ -3,18 +3,23 @@
 //   C = conj(K) FFT2(y) / (sigma^2 D) / (H W),  G = alpha / D / (H W),
 //   D = |K|^2 / sigma^2 + alpha,  K = FFT2 of the circularly centred PSF.
 //
-// The 2-D transform is three passes over a half spectrum (H x (W/2 + 1) complex):
-//   1. rows, real-to-complex: each row of W reals is packed as W/2 complex values, a
-//      W/2-point complex FFT is taken and the W/2 + 1 non-redundant bins are untangled;
-//   2. columns: forward FFT of each column, the pointwise solve X = C + G F, inverse FFT
-//      (all in shared memory, one read and one write of the spectrum);
-//   3. rows, complex-to-real, with the relative-change statistics of the FP step
-//      (sum (x_{k+1} - x_k)^2, sum x_k^2) reduced on the fly and, in a batched solve, the
-//      termination test of the problem done by the last CTA to finish it.
-// Transforms are self-sorting Stockham passes in shared memory with radix 4, 2 and 3
-// (sizes 2^a 3^b), twiddles from tables computed on the host in double precision.
-// Inverse transforms use IFFT(X) = conj(FFT(conj(X))); the 1/(H W) scale is folded
-// into C and G.
+// The 2-D transform works on a half spectrum (H x (W/2 + 1) complex):
+//   rows, real-to-complex: each row of W reals is packed as W/2 complex values, a
+//     W/2-point complex FFT is taken and the W/2 + 1 non-redundant bins are untangled;
+//   columns: forward FFT, the pointwise solve X = C + G F, inverse FFT;
+//   rows, complex-to-real, with the relative-change statistics of the FP step.
+// Two implementations with bitwise identical arithmetic:
+//   * k_fft_solve_cluster: one thread-block cluster per problem, the half spectrum in the
+//     cluster's shared memory, transposed through distributed shared memory (images up
+//     to 512 x 512);
+//   * k_fft_r2c / k_fft_cols / k_fft_c2r: three passes through global memory (any size).
+// Transforms are self-sorting Stockham passes in shared memory with register-resident
+// radix 16, 12, 8, 6, 4, 3 and 2 butterflies (sizes 2^a 3^b): few passes, so few
+// barriers. Composite radices are built from radix-2/3/4 kernels with constant roots of
+// unity; pass twiddles come from tables computed on the host in double precision.
+// Sequences in shared memory are padded (one slot per 16 elements, odd stride) so the
+// strided Stockham writes and the column transposes are free of bank conflicts.
+// Inverse transforms use IFFT(X) = conj(FFT(conj(X))); the 1/(H W) scale is in C and G.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -37,17 +42,190 @@ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.
 __device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); }  // * (+i)
 
 // Division by a run-time invariant d < 2^16 for numerators t < 2^16: q = hi32(t * m) with
-// m = floor(2^32 / d) + 1 (exact in that range; d = 1 handled separately). Replaces the
-// integer divisions of the index arithmetic, which otherwise dominate the FFT kernels.
+// m = floor(2^32 / d) + 1 (exact in that range; d = 1 handled separately). Every index
+// divided here is below 2^16 (image sides <= 2048, <= 16 sequences per CTA).
 struct FastDiv {
   uint32_t d, m;
-  __device__ __forceinline__ explicit FastDiv(int dd) : d((uint32_t)dd), m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
+  __device__ __forceinline__ explicit FastDiv(int dd)
+      : d((uint32_t)dd), m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
   __device__ __forceinline__ int div(int t) const { return d == 1 ? t : (int)__umulhi((uint32_t)t, m); }
   __device__ __forceinline__ void divmod(int t, int &q, int &r) const {
     q = div(t);
     r = t - q * (int)d;
   }
 };
+
+// e^{-2 pi i m / 48}: every root of unity the radix-16/12/8/6 kernels need
+__device__ __forceinline__ float2 root48(int m) {
+  constexpr float c[48] = {
+      1.0f, 0.99144486137381038f, 0.96592582628906831f, 0.92387953251128674f,
+      0.8660254037844386f, 0.79335334029123517f, 0.70710678118654757f, 0.60876142900872066f,
+      0.5f, 0.38268343236508978f, 0.25881904510252074f, 0.1305261922200516f,
+      0.0f, -0.1305261922200516f, -0.25881904510252074f, -0.38268343236508978f,
+      -0.5f, -0.60876142900872066f, -0.70710678118654757f, -0.79335334029123517f,
+      -0.8660254037844386f, -0.92387953251128674f, -0.96592582628906831f, -0.99144486137381038f,
+      -1.0f, -0.99144486137381038f, -0.96592582628906831f, -0.92387953251128674f,
+      -0.8660254037844386f, -0.79335334029123517f, -0.70710678118654757f, -0.60876142900872066f,
+      -0.5f, -0.38268343236508978f, -0.25881904510252074f, -0.1305261922200516f,
+      0.0f, 0.1305261922200516f, 0.25881904510252074f, 0.38268343236508978f,
+      0.5f, 0.60876142900872066f, 0.70710678118654757f, 0.79335334029123517f,
+      0.8660254037844386f, 0.92387953251128674f, 0.96592582628906831f, 0.99144486137381038f};
+  constexpr float s[48] = {
+      0.0f, 0.1305261922200516f, 0.25881904510252074f, 0.38268343236508978f,
+      0.5f, 0.60876142900872066f, 0.70710678118654757f, 0.79335334029123517f,
+      0.8660254037844386f, 0.92387953251128674f, 0.96592582628906831f, 0.99144486137381038f,
+      1.0f, 0.99144486137381038f, 0.96592582628906831f, 0.92387953251128674f,
+      0.8660254037844386f, 0.79335334029123517f, 0.70710678118654757f, 0.60876142900872066f,
+      0.5f, 0.38268343236508978f, 0.25881904510252074f, 0.1305261922200516f,
+      0.0f, -0.1305261922200516f, -0.25881904510252074f, -0.38268343236508978f,
+      -0.5f, -0.60876142900872066f, -0.70710678118654757f, -0.79335334029123517f,
+      -0.8660254037844386f, -0.92387953251128674f, -0.96592582628906831f, -0.99144486137381038f,
+      -1.0f, -0.99144486137381038f, -0.96592582628906831f, -0.92387953251128674f,
+      -0.8660254037844386f, -0.79335334029123517f, -0.70710678118654757f, -0.60876142900872066f,
+      -0.5f, -0.38268343236508978f, -0.25881904510252074f, -0.1305261922200516f};
+  return make_float2(c[m % 48], -s[m % 48]);
+}
+
+// In-register forward DFTs (natural-order output).
+__device__ __forceinline__ void dft_base(float2 (&a)[2]) {
+  const float2 t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+__device__ __forceinline__ void dft_base(float2 (&a)[3]) {
+  // w = e^{-2 pi i / 3}: y1 = a0 - s/2 - i (sqrt3/2) d, y2 = a0 - s/2 + i (sqrt3/2) d
+  const float2 s12 = cadd(a[1], a[2]), d12 = csub(a[1], a[2]);
+  const float2 m = make_float2(a[0].x - 0.5f * s12.x, a[0].y - 0.5f * s12.y);
+  const float h = 0.86602540378443864676f;
+  const float2 e = make_float2(h * d12.x, h * d12.y);
+  a[0] = cadd(a[0], s12);
+  a[1] = cadd(m, mul_mi(e));
+  a[2] = cadd(m, mul_pi(e));
+}
+__device__ __forceinline__ void dft_base(float2 (&a)[4]) {
+  const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]), t2 = cadd(a[1], a[3]);
+  const float2 t3 = mul_mi(csub(a[1], a[3]));
+  a[0] = cadd(t0, t2);
+  a[1] = cadd(t1, t3);
+  a[2] = csub(t0, t2);
+  a[3] = csub(t1, t3);
+}
+
+// N = A * B point DFT by one Cooley-Tukey step: B-point DFTs of the A interleaved
+// subsequences, twiddles w_N^{n1 k1}, A-point DFTs across them; X[k1 + B k2].
+template <int A, int B>
+__device__ __forceinline__ void dft_ab(float2 (&x)[A * B]) {
+  constexpr int N = A * B;
+  float2 y[A][B];
+#pragma unroll
+  for (int n1 = 0; n1 < A; ++n1) {
+    float2 t[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) t[n2] = x[n1 + A * n2];
+    dft_base(t);
+#pragma unroll
+    for (int k1 = 0; k1 < B; ++k1) {
+      const int m = (n1 * k1) % N;
+      if (m == 0)
+        y[n1][k1] = t[k1];
+      else if (4 * m == N)
+        y[n1][k1] = mul_mi(t[k1]);
+      else if (2 * m == N)
+        y[n1][k1] = make_float2(-t[k1].x, -t[k1].y);
+      else
+        y[n1][k1] = cmul(t[k1], root48(m * (48 / N)));
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < B; ++k1) {
+    float2 t[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) t[n1] = y[n1][k1];
+    dft_base(t);
+#pragma unroll
+    for (int k2 = 0; k2 < A; ++k2) x[k1 + B * k2] = t[k2];
+  }
+}
+
+template <int R> __device__ __forceinline__ void dft(float2 (&a)[R]);
+template <> __device__ __forceinline__ void dft<2>(float2 (&a)[2]) { dft_base(a); }
+template <> __device__ __forceinline__ void dft<3>(float2 (&a)[3]) { dft_base(a); }
+template <> __device__ __forceinline__ void dft<4>(float2 (&a)[4]) { dft_base(a); }
+template <> __device__ __forceinline__ void dft<6>(float2 (&a)[6]) { dft_ab<2, 3>(a); }
+template <> __device__ __forceinline__ void dft<8>(float2 (&a)[8]) { dft_ab<2, 4>(a); }
+template <> __device__ __forceinline__ void dft<12>(float2 (&a)[12]) { dft_ab<4, 3>(a); }
+template <> __device__ __forceinline__ void dft<16>(float2 (&a)[16]) { dft_ab<4, 4>(a); }
+
+// padded position of element e of a shared-memory sequence (one pad slot per 16)
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+
+// One Stockham pass of radix R over nseq sequences (stride ss) of length n, after passes
+// of product Ns: butterfly j reads elements j + q n/R, twiddles them by
+// w_n^{(j mod Ns) q n/(Ns R)}, takes an R-point DFT and writes positions
+// (j - j mod Ns) R + j mod Ns + q Ns (natural-order output overall).
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2 *in, float2 *out, int n, int nseq, int ss,
+                                              int Ns, const float2 *__restrict__ tw, int tid,
+                                              int nthr) {
+  const int nb = n / R;
+  const int tws = n / (Ns * R);
+  const FastDiv dnb(nb), dns(Ns);
+  for (int t = tid; t < nseq * nb; t += nthr) {
+    int s, j, g, kk;
+    dnb.divmod(t, s, j);
+    dns.divmod(j, g, kk);
+    const float2 *src = in + s * ss;
+    float2 *dst = out + s * ss;
+    float2 a[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[q] = src[pidx(j + q * nb)];
+    if (kk) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[kk * q * tws]);
+    }
+    dft<R>(a);
+    const int base = g * Ns * R + kk;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[pidx(base + q * Ns)] = a[q];
+  }
+}
+
+__device__ __forceinline__ int pick_radix(int rem) {
+  if (rem % 16 == 0) return 16;
+  if (rem % 12 == 0) return 12;
+  if (rem % 8 == 0) return 8;
+  if (rem % 6 == 0) return 6;
+  if (rem % 4 == 0) return 4;
+  if (rem % 3 == 0) return 3;
+  return 2;
+}
+
+// Forward FFT of nseq padded sequences of length n (2^a 3^b) held at x + s * ss; ping-pongs
+// between x and y and returns the buffer holding the result. Ends with a barrier.
+__device__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, int ss,
+                            const float2 *__restrict__ tw, int tid, int nthr) {
+  float2 *in = x, *out = y;
+  int Ns = 1, rem = n;
+  while (rem > 1) {
+    const int r = pick_radix(rem);
+    switch (r) {
+      case 16: stockham_pass<16>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      case 12: stockham_pass<12>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      case 8: stockham_pass<8>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      case 6: stockham_pass<6>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      case 4: stockham_pass<4>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      case 3: stockham_pass<3>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      default: stockham_pass<2>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+    }
+    __syncthreads();
+    float2 *tmp = in;
+    in = out;
+    out = tmp;
+    Ns *= r;
+    rem /= r;
+  }
+  return in;
+}
 
 // Copies `total` elements with U independent loads in flight per thread (load all, then
 // store all), instead of one load-to-use round trip per loop iteration.
@@ -68,76 +246,82 @@ __device__ __forceinline__ void copy_batched(int total, int tid, int nthr, Load 
   }
 }
 
-// Forward Stockham FFT of `nseq` sequences of length n held in shared memory (sequence s
-// at x + s * ss). Ping-pongs between x and y; returns the buffer holding the result.
-// Pass with radix r after previous passes of product Ns: butterfly j reads elements
-// j + q n/r, twiddles them by w_n^{(j mod Ns) q n/(Ns r)}, takes an r-point DFT and writes
-// to (j - j mod Ns) r + j mod Ns + q Ns (natural order output).
-__device__ float2 *stockham(float2 *x, float2 *y, int n, int nseq, int ss,
-                            const float2 *__restrict__ tw, int tid, int nthr) {
-  float2 *in = x, *out = y;
-  int Ns = 1;
-  int rem = n;
-  while (rem > 1) {
-    const int r = (rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3);
-    const int nb = n / r;
-    const int tws = n / (Ns * r);
-    const int total = nseq * nb;
-    const FastDiv dnb(nb), dns(Ns);
-    for (int t = tid; t < total; t += nthr) {
-      int s, j, g, kk;
-      dnb.divmod(t, s, j);
-      dns.divmod(j, g, kk);
-      const float2 *src = in + s * ss;
-      float2 *dst = out + s * ss;
-      const int base = g * Ns * r + kk;
-      if (r == 4) {
-        float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb], a3 = src[j + 3 * nb];
-        if (kk) {
-          const int ti = kk * tws;
-          a1 = cmul(a1, tw[ti]);
-          a2 = cmul(a2, tw[2 * ti]);
-          a3 = cmul(a3, tw[3 * ti]);
-        }
-        const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
-        const float2 t3 = mul_mi(csub(a1, a3));
-        dst[base] = cadd(t0, t2);
-        dst[base + Ns] = cadd(t1, t3);
-        dst[base + 2 * Ns] = csub(t0, t2);
-        dst[base + 3 * Ns] = csub(t1, t3);
-      } else if (r == 2) {
-        float2 a0 = src[j], a1 = src[j + nb];
-        if (kk) a1 = cmul(a1, tw[kk * tws]);
-        dst[base] = cadd(a0, a1);
-        dst[base + Ns] = csub(a0, a1);
-      } else {
-        float2 a0 = src[j], a1 = src[j + nb], a2 = src[j + 2 * nb];
-        if (kk) {
-          const int ti = kk * tws;
-          a1 = cmul(a1, tw[ti]);
-          a2 = cmul(a2, tw[2 * ti]);
-        }
-        // w = e^{-2 pi i / 3}: y1 = a0 - s/2 - i (sqrt3/2) d, y2 = a0 - s/2 + i (sqrt3/2) d
-        const float2 s12 = cadd(a1, a2), d12 = csub(a1, a2);
-        const float2 m = make_float2(a0.x - 0.5f * s12.x, a0.y - 0.5f * s12.y);
-        const float h = 0.86602540378443864676f;
-        const float2 e = make_float2(h * d12.x, h * d12.y);
-        dst[base] = cadd(a0, s12);
-        dst[base + Ns] = cadd(m, mul_mi(e));
-        dst[base + 2 * Ns] = cadd(m, mul_pi(e));
-      }
-    }
-    __syncthreads();
-    float2 *tmp = in;
-    in = out;
-    out = tmp;
-    Ns *= r;
-    rem /= r;
-  }
-  return in;
+// Bin k of the half spectrum from the packed M-point transform Z of one row (padded):
+// X_k = ((Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k})) / 2, w = e^{-2 pi i / W}.
+__device__ __forceinline__ float2 r2c_bin(const float2 *Z, int M, int kk, const float2 *tww) {
+  const float2 zk = Z[pidx(kk == M ? 0 : kk)];
+  const float2 zc = cconj(Z[pidx(kk == 0 ? 0 : M - kk)]);
+  const float2 t = cmul(tww[kk], csub(zk, zc));
+  const float2 s = cadd(zk, zc);
+  return make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
 }
 
-// Pass 1: rows, real to half spectrum. Item (prob, first row).
+// conj(2 Z_k) with 2 Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) e^{+2 pi i k / W}:
+// the forward transform of it, conjugated, is W times the row's real samples (packed).
+__device__ __forceinline__ float2 c2r_pre(float2 xk, float2 xmk, float2 twk) {
+  const float2 xc = cconj(xmk);
+  const float2 e = cadd(xk, xc);
+  const float2 o = cmul(csub(xk, xc), cconj(twk));
+  return cconj(cadd(e, mul_pi(o)));
+}
+
+// Writes of x_{k+1} and the relative-change statistics against x_k.
+struct StepOut {
+  const ProbDev *P;
+  StepArgs sa;
+  void *dst_ring;
+  const void *src_ring;
+  int src_bf16;
+  __device__ __forceinline__ void init(const ProbDev *p, const StepArgs &s) {
+    P = p;
+    sa = s;
+    const int esz = P->storage ? 2 : 4;
+    dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
+    src_ring = sa.src_ptr ? sa.src_ptr
+                          : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
+    src_bf16 = sa.src_ptr ? 0 : P->storage;
+  }
+  __device__ __forceinline__ float2 prev(long base) const {
+    return make_float2(load_img(src_ring, base, src_bf16), load_img(src_ring, base + 1, src_bf16));
+  }
+  // writes x_{k+1}[base], [base+1] = (xe, xo); accumulates the statistics against pv
+  __device__ __forceinline__ void put(long base, float xe, float xo, float2 pv, float &sd,
+                                      float &sx) const {
+    float ye = xe, yo = xo;
+    if (sa.dst_ptr) {
+      *reinterpret_cast<float2 *>(sa.dst_ptr + base) = make_float2(xe, xo);
+    } else {
+      store_img(dst_ring, base, xe, P->storage);
+      store_img(dst_ring, base + 1, xo, P->storage);
+      if (P->storage) {
+        ye = __bfloat162float(__float2bfloat16_rn(xe));
+        yo = __bfloat162float(__float2bfloat16_rn(xo));
+      }
+    }
+    sd = fmaf(ye - pv.x, ye - pv.x, sd);
+    sd = fmaf(yo - pv.y, yo - pv.y, sd);
+    sx = fmaf(pv.x, pv.x, sx);
+    sx = fmaf(pv.y, pv.y, sx);
+  }
+};
+
+// Termination test of Algorithm 3 after an FP step (one thread).
+__device__ __forceinline__ void finish_step(ProbState *st, double sd, double sx, int dst_slot) {
+  const double rel = sx > 0.0 ? sqrt(sd / sx) : (sd > 0.0 ? INFINITY : 0.0);
+  st->rel_change = rel;
+  st->calls += 1;
+  if (rel < st->tol || st->calls >= st->max_calls) {
+    st->done = 1;
+    st->converged = rel < st->tol ? 1 : 0;
+    st->final_slot = dst_slot;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// three-pass path
+// ---------------------------------------------------------------------------------------
+
+// Pass 1: rows, real to half spectrum. Item (prob, first row, rows).
 __global__ void __launch_bounds__(256)
 k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
           int buf_cap, const float *src_override, float2 *dst_override, int skip_done) {
@@ -146,6 +330,7 @@ k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   const ProbDev *P = probs + it.prob;
   if (skip_done && P->st->done) return;
   const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
+  const int ss = fft_seq_stride(M);
   const int r0 = it.a;
   const int nr = min(it.b, H - r0);
   float2 *twm = sm;
@@ -156,25 +341,25 @@ k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   const float *src = src_override ? src_override : P->f;
-  const FastDiv fd1(M > 0 ? M : 1);
-  for (int idx = tid; idx < nr * M; idx += nthr) {
-    int row, n;
-    fd1.divmod(idx, row, n);
-    b0[row * M + n] = reinterpret_cast<const float2 *>(src + (long)(r0 + row) * W)[n];
-  }
+  const FastDiv dm(M), dwh(Wh);
+  copy_batched<4>(nr * M, tid, nthr,
+      [&](int idx) {
+        int row, n;
+        dm.divmod(idx, row, n);
+        return reinterpret_cast<const float2 *>(src + (long)(r0 + row) * W)[n];
+      },
+      [&](int idx, float2 v) {
+        int row, n;
+        dm.divmod(idx, row, n);
+        b0[row * ss + pidx(n)] = v;
+      });
   __syncthreads();
-  const float2 *Z = stockham(b0, b1, M, nr, M, twm, tid, nthr);
+  const float2 *Z = fft_smem(b0, b1, M, nr, ss, twm, tid, nthr);
   float2 *dst = dst_override ? dst_override : P->spec;
-  const FastDiv fd2(Wh > 0 ? Wh : 1);
   for (int idx = tid; idx < nr * Wh; idx += nthr) {
     int row, kk;
-    fd2.divmod(idx, row, kk);
-    const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
-    const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
-    // X_k = ((Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k})) / 2
-    const float2 t = cmul(tww[kk], csub(zk, zc));
-    const float2 sum = cadd(zk, zc);
-    dst[(long)(r0 + row) * Wh + kk] = make_float2(0.5f * (sum.x + t.y), 0.5f * (sum.y - t.x));
+    dwh.divmod(idx, row, kk);
+    dst[(long)(r0 + row) * Wh + kk] = r2c_bin(Z + row * ss, M, kk, tww);
   }
 }
 
@@ -191,65 +376,63 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   const int H = P->H, Wh = P->Wh;
   const int c0 = it.a;
   const int nc = min(it.b, Wh - c0);
-  const int hs = H + 1;   // padded column stride in shared memory
+  const int hs = fft_seq_stride(H);
   float2 *twh = sm;
   float2 *b0 = twh + tw_cap;
   float2 *b1 = b0 + buf_cap;
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   float2 *spec = spec_override ? spec_override : P->spec;
-  const FastDiv fd3(nc > 0 ? nc : 1);
-  for (int idx = tid; idx < H * nc; idx += nthr) {
-    int r, c;
-    fd3.divmod(idx, r, c);
-    b0[c * hs + r] = spec[(long)r * Wh + c0 + c];
-  }
+  const FastDiv dnc(nc > 0 ? nc : 1);
+  copy_batched<4>(H * nc, tid, nthr,
+      [&](int idx) {
+        int r, c;
+        dnc.divmod(idx, r, c);
+        return spec[(long)r * Wh + c0 + c];
+      },
+      [&](int idx, float2 v) {
+        int r, c;
+        dnc.divmod(idx, r, c);
+        b0[c * hs + pidx(r)] = v;
+      });
   __syncthreads();
-  float2 *F = stockham(b0, b1, H, nc, hs, twh, tid, nthr);
+  float2 *F = fft_smem(b0, b1, H, nc, hs, twh, tid, nthr);
   if (mode == 0) {
-    const FastDiv fd4(nc > 0 ? nc : 1);
     for (int idx = tid; idx < H * nc; idx += nthr) {
       int r, c;
-      fd4.divmod(idx, r, c);
-      spec[(long)r * Wh + c0 + c] = F[c * hs + r];
+      dnc.divmod(idx, r, c);
+      spec[(long)r * Wh + c0 + c] = F[c * hs + pidx(r)];
     }
     return;
   }
-  if (mode == 1) {
-    const FastDiv fd5(nc > 0 ? nc : 1);
-    for (int idx = tid; idx < H * nc; idx += nthr) {
-      int r, c;
-      fd5.divmod(idx, r, c);
-      const long g = (long)r * Wh + c0 + c;
-      const float2 cc = P->Cc[g];
-      const float gg = P->Gg[g];
-      const float2 f = F[c * hs + r];
-      F[c * hs + r] = make_float2(fmaf(gg, f.x, cc.x), -fmaf(gg, f.y, cc.y));  // conj(C + G F)
-    }
-  } else {
-    // mode 2: H x for the objective: conj(K F / (H W))
-    const float inv_hw = 1.0f / ((float)H * (float)P->W);
-    const FastDiv fd6(nc > 0 ? nc : 1);
-    for (int idx = tid; idx < H * nc; idx += nthr) {
-      int r, c;
-      fd6.divmod(idx, r, c);
-      const float2 kk = P->Kh[(long)r * Wh + c0 + c];
-      const float2 v = cmul(kk, F[c * hs + r]);
-      F[c * hs + r] = make_float2(v.x * inv_hw, -v.y * inv_hw);
-    }
-  }
-  __syncthreads();
-  float2 *other = (F == b0) ? b1 : b0;
-  const float2 *X = stockham(F, other, H, nc, hs, twh, tid, nthr);
-  const FastDiv fd7(nc > 0 ? nc : 1);
+  const float inv_hw = 1.0f / ((float)H * (float)P->W);
   for (int idx = tid; idx < H * nc; idx += nthr) {
     int r, c;
-    fd7.divmod(idx, r, c);
-    spec[(long)r * Wh + c0 + c] = cconj(X[c * hs + r]);
+    dnc.divmod(idx, r, c);
+    const long g = (long)r * Wh + c0 + c;
+    const float2 fv = F[c * hs + pidx(r)];
+    float2 xv;
+    if (mode == 1) {
+      const float2 cc = P->Cc[g];
+      const float gg = P->Gg[g];
+      xv = make_float2(fmaf(gg, fv.x, cc.x), fmaf(gg, fv.y, cc.y));
+    } else {
+      const float2 kv = cmul(P->Kh[g], fv);
+      xv = make_float2(kv.x * inv_hw, kv.y * inv_hw);
+    }
+    F[c * hs + pidx(r)] = cconj(xv);
+  }
+  __syncthreads();
+  const float2 *X = fft_smem(F, F == b0 ? b1 : b0, H, nc, hs, twh, tid, nthr);
+  for (int idx = tid; idx < H * nc; idx += nthr) {
+    int r, c;
+    dnc.divmod(idx, r, c);
+    spec[(long)r * Wh + c0 + c] = cconj(X[c * hs + pidx(r)]);
   }
 }
 
-// Pass 3: rows, half spectrum to real, with the FP-step statistics.
+// Pass 3: rows, half spectrum to real, with the FP-step statistics and (batched solves)
+// the termination test by the last CTA of the problem.
 __global__ void __launch_bounds__(256)
 k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
           int buf_cap, StepArgs sa) {
@@ -259,6 +442,7 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   const ProbDev *P = probs + it.prob;
   if (sa.update_state && P->st->done) return;
   const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
+  const int ss = fft_seq_stride(M);
   const int r0 = it.a;
   const int nr = min(it.b, H - r0);
   float2 *twm = sm;
@@ -270,51 +454,25 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   __syncthreads();
   const float2 *spec = P->spec;
-  const FastDiv fd8(M > 0 ? M : 1);
+  const FastDiv dm(M);
   for (int idx = tid; idx < nr * M; idx += nthr) {
     int row, kk;
-    fd8.divmod(idx, row, kk);
-    const float2 xk = spec[(long)(r0 + row) * Wh + kk];
-    const float2 xc = cconj(spec[(long)(r0 + row) * Wh + (M - kk)]);
-    // 2 E_k = X_k + conj X_{M-k};  2 O_k = (X_k - conj X_{M-k}) e^{+2 pi i k / W}
-    const float2 e = cadd(xk, xc);
-    const float2 o = cmul(csub(xk, xc), cconj(tww[kk]));
-    const float2 z = cadd(e, mul_pi(o));          // 2 Z_k = 2 E_k + i 2 O_k
-    b0[row * M + kk] = cconj(z);
+    dm.divmod(idx, row, kk);
+    const float2 *xr = spec + (long)(r0 + row) * Wh;
+    b0[row * ss + pidx(kk)] = c2r_pre(xr[kk], xr[M - kk], tww[kk]);
   }
   __syncthreads();
-  const float2 *Y = stockham(b0, b1, M, nr, M, twm, tid, nthr);
+  const float2 *Y = fft_smem(b0, b1, M, nr, ss, twm, tid, nthr);
 
-  // output row = conj(Y); x[2n] = Re, x[2n+1] = Im; statistics against x_in
-  const int esz = P->storage ? 2 : 4;
-  float *dst = sa.dst_ptr ? sa.dst_ptr : nullptr;
-  void *dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
-  const void *src_ring = sa.src_ptr ? sa.src_ptr
-                                    : static_cast<const char *>(P->ring) +
-                                          (size_t)sa.src * P->slot_stride * esz;
-  const int src_bf16 = sa.src_ptr ? 0 : P->storage;
+  StepOut out;
+  out.init(P, sa);
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   for (int row = warp; row < nr; row += nwarps) {
     const long rowbase = (long)(r0 + row) * W;
     float sd = 0.f, sx = 0.f;
     for (int n = lane; n < M; n += 32) {
-      const float2 v = Y[row * M + n];
-      const float xe = v.x, xo = -v.y;
-      if (dst) {
-        reinterpret_cast<float2 *>(dst + rowbase)[n] = make_float2(xe, xo);
-      } else {
-        store_img(dst_ring, rowbase + 2 * n, xe, P->storage);
-        store_img(dst_ring, rowbase + 2 * n + 1, xo, P->storage);
-      }
-      // statistics use the stored (rounded) values of the new iterate
-      const float ye = P->storage ? __bfloat162float(__float2bfloat16_rn(xe)) : xe;
-      const float yo = P->storage ? __bfloat162float(__float2bfloat16_rn(xo)) : xo;
-      const float pe = load_img(src_ring, rowbase + 2 * n, src_bf16);
-      const float po = load_img(src_ring, rowbase + 2 * n + 1, src_bf16);
-      sd = fmaf(ye - pe, ye - pe, sd);
-      sd = fmaf(yo - po, yo - po, sd);
-      sx = fmaf(pe, pe, sx);
-      sx = fmaf(po, po, sx);
+      const float2 v = Y[row * ss + pidx(n)];
+      out.put(rowbase + 2 * n, v.x, -v.y, out.prev(rowbase + 2 * n), sd, sx);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -325,7 +483,6 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   }
   if (!sa.update_state) return;
 
-  // last CTA of this problem: fixed-order reduction of the row sums, termination test
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -347,22 +504,18 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
   }
   if (lane == 0) {
-    ProbState *st = P->st;
-    const double rel = sx > 0.0 ? sqrt(sd / sx) : (sd > 0.0 ? INFINITY : 0.0);
-    st->rel_change = rel;
-    st->calls += 1;
-    if (rel < st->tol || st->calls >= st->max_calls) {
-      st->done = 1;
-      st->converged = rel < st->tol ? 1 : 0;
-      st->final_slot = sa.dst;
-    }
-    st->counter = 0;
+    finish_step(P->st, sd, sx, sa.dst);
+    P->st->counter = 0;
     __threadfence();
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// cluster path
+// ---------------------------------------------------------------------------------------
+
 // The whole solve of one FP step for one problem in one thread-block cluster, with the
-// half spectrum held in the cluster's shared memory (used when it fits):
+// half spectrum held in the cluster's shared memory:
 //   rows R2C of the CTA's row band -> A (rows x (W/2+1), local shared memory)
 //   cluster barrier; each CTA gathers its band of spectrum columns from every CTA's A
 //   through distributed shared memory, column FFT, X = C + G F, inverse column FFT
@@ -370,28 +523,29 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
 //   cluster barrier; rows C2R of the band -> x_{k+1}, statistics, termination test.
 // Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
 // x_{k+1} (4 B); the spectrum never leaves the chip.
+constexpr int kClusterThreads = 512;
+
 __device__ __forceinline__ int band_lo(int q, int n, const FastDiv &by_ncta) { return by_ncta.div(q * n); }
 __device__ __forceinline__ int band_owner(int h, int ncta, const FastDiv &by_n) {
   return by_n.div((h + 1) * ncta - 1);
 }
-
-constexpr int kClusterThreads = 512;
 
 __global__ void __launch_bounds__(kClusterThreads)
 k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ list, StepArgs sa,
                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
   extern __shared__ float2 sm[];
   __shared__ float part_d, part_x;
+  __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
   const ProbDev *P = probs + list[blockIdx.x / ncta];
   if (sa.update_state && P->st->done) return;   // uniform over the cluster
   const int H = P->H, W = P->W, M = P->M, Wh = P->Wh;
+  const int ssm = fft_seq_stride(M), ssh = fft_seq_stride(H);
   const FastDiv by_ncta(ncta), by_h(H);
   const int r0 = band_lo(rank, H, by_ncta), nr = band_lo(rank + 1, H, by_ncta) - r0;
   const int c0 = band_lo(rank, Wh, by_ncta), nc = band_lo(rank + 1, Wh, by_ncta) - c0;
-  const int hs = H + 1;
   float2 *twm = sm;
   float2 *tww = twm + tw_cap_m;
   float2 *twh = tww + tw_cap_m + 1;
@@ -402,30 +556,42 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
+  const FastDiv fdm(M), fdwh(Wh), fdc(nc > 0 ? nc : 1);
+  // x_k for the statistics, fetched first (its latency hides behind the transforms)
+  constexpr int kPrev = 4;
+  float2 prev[kPrev];
+  StepOut out;
+  out.init(P, sa);
+#pragma unroll
+  for (int u = 0; u < kPrev; ++u) {
+    const int idx = tid + u * nthr;
+    if (idx < nr * M) {
+      int row, n;
+      fdm.divmod(idx, row, n);
+      prev[u] = out.prev((long)(r0 + row) * W + 2 * n);
+    }
+  }
   // 1. rows of f, real to half spectrum
-  const FastDiv fdm(M);
   copy_batched<4>(nr * M, tid, nthr,
       [&](int idx) {
         int row, n;
         fdm.divmod(idx, row, n);
         return reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
       },
-      [&](int idx, float2 v) { X0[idx] = v; });
+      [&](int idx, float2 v) {
+        int row, n;
+        fdm.divmod(idx, row, n);
+        X0[row * ssm + pidx(n)] = v;
+      });
   __syncthreads();
-  const float2 *Z = stockham(X0, X1, M, nr, M, twm, tid, nthr);
-  const FastDiv fd10(Wh > 0 ? Wh : 1);
+  const float2 *Z = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
   for (int idx = tid; idx < nr * Wh; idx += nthr) {
     int row, kk;
-    fd10.divmod(idx, row, kk);
-    const float2 zk = Z[row * M + (kk == M ? 0 : kk)];
-    const float2 zc = cconj(Z[row * M + (kk == 0 ? 0 : M - kk)]);
-    const float2 t = cmul(tww[kk], csub(zk, zc));
-    const float2 s = cadd(zk, zc);
-    A[row * Wh + kk] = make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
+    fdwh.divmod(idx, row, kk);
+    A[row * Wh + kk] = r2c_bin(Z + row * ssm, M, kk, tww);
   }
   cl.sync();
   // 2. gather this CTA's spectrum columns from every row band
-  const FastDiv fdc(nc > 0 ? nc : 1);
   copy_batched<8>(H * nc, tid, nthr,
       [&](int idx) {
         int h, c;
@@ -437,10 +603,10 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       [&](int idx, float2 v) {
         int h, c;
         fdc.divmod(idx, h, c);
-        X0[c * hs + h] = v;
+        X0[c * ssh + pidx(h)] = v;
       });
   __syncthreads();
-  float2 *F = stockham(X0, X1, H, nc, hs, twh, tid, nthr);
+  float2 *F = fft_smem(X0, X1, H, nc, ssh, twh, tid, nthr);
   for (int base = tid; base < H * nc; base += 4 * nthr) {
     float2 cc[4];
     float gg[4];
@@ -461,96 +627,75 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       if (idx < H * nc) {
         int r, c;
         fdc.divmod(idx, r, c);
-        const float2 fv = F[c * hs + r];
-        F[c * hs + r] = make_float2(fmaf(gg[u], fv.x, cc[u].x), -fmaf(gg[u], fv.y, cc[u].y));  // conj(C + G F)
+        const float2 fv = F[c * ssh + pidx(r)];
+        F[c * ssh + pidx(r)] = make_float2(fmaf(gg[u], fv.x, cc[u].x), -fmaf(gg[u], fv.y, cc[u].y));
       }
     }
   }
   __syncthreads();
-  const float2 *Xs = stockham(F, F == X0 ? X1 : X0, H, nc, hs, twh, tid, nthr);
+  const float2 *Xs = fft_smem(F, F == X0 ? X1 : X0, H, nc, ssh, twh, tid, nthr);
   cl.sync();   // every CTA has finished reading the A bands
   // 3. scatter the solved columns back to the row bands
-  const FastDiv fd13(nc > 0 ? nc : 1);
   for (int idx = tid; idx < H * nc; idx += nthr) {
     int h, c;
-    fd13.divmod(idx, h, c);
+    fdc.divmod(idx, h, c);
     const int q = band_owner(h, ncta, by_h);
     float2 *Aq = cl.map_shared_rank(A, q);
-    Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c] = cconj(Xs[c * hs + h]);
+    Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c] = cconj(Xs[c * ssh + pidx(h)]);
   }
   cl.sync();
   // 4. rows, half spectrum to real, statistics against x_k
-  const FastDiv fd14(M > 0 ? M : 1);
   for (int idx = tid; idx < nr * M; idx += nthr) {
     int row, kk;
-    fd14.divmod(idx, row, kk);
-    const float2 xk = A[row * Wh + kk];
-    const float2 xc = cconj(A[row * Wh + (M - kk)]);
-    const float2 e = cadd(xk, xc);
-    const float2 o = cmul(csub(xk, xc), cconj(tww[kk]));
-    X0[row * M + kk] = cconj(cadd(e, mul_pi(o)));
+    fdm.divmod(idx, row, kk);
+    X0[row * ssm + pidx(kk)] = c2r_pre(A[row * Wh + kk], A[row * Wh + (M - kk)], tww[kk]);
   }
   __syncthreads();
-  const float2 *Y = stockham(X0, X1, M, nr, M, twm, tid, nthr);
-  const int esz = P->storage ? 2 : 4;
-  void *dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
-  const void *src_ring = sa.src_ptr ? sa.src_ptr
-                                    : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
-  const int src_bf16 = sa.src_ptr ? 0 : P->storage;
+  const float2 *Y = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
   float sd = 0.f, sx = 0.f;
-  // previous iterate x_k for the statistics: 4 pixel pairs in flight per thread
-  for (int b0 = tid; b0 < nr * M; b0 += 4 * nthr) {
-    float2 prev[4];
+  for (int b0 = tid; b0 < nr * M; b0 += kPrev * nthr) {
+    float2 pv[kPrev];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kPrev; ++u) {
       const int idx = b0 + u * nthr;
       if (idx < nr * M) {
-        int row, n;
-        fdm.divmod(idx, row, n);
-        const long base = (long)(r0 + row) * W + 2 * n;
-        prev[u] = make_float2(load_img(src_ring, base, src_bf16), load_img(src_ring, base + 1, src_bf16));
+        if (b0 == tid) {
+          pv[u] = prev[u];
+        } else {
+          int row, n;
+          fdm.divmod(idx, row, n);
+          pv[u] = out.prev((long)(r0 + row) * W + 2 * n);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kPrev; ++u) {
       const int idx = b0 + u * nthr;
       if (idx >= nr * M) break;
       int row, n;
       fdm.divmod(idx, row, n);
-      const long base = (long)(r0 + row) * W + 2 * n;
-      const float2 v = Y[row * M + n];
-      const float xe = v.x, xo = -v.y;
-      float ye = xe, yo = xo;
-      if (sa.dst_ptr) {
-        reinterpret_cast<float2 *>(sa.dst_ptr + (long)(r0 + row) * W)[n] = make_float2(xe, xo);
-      } else {
-        store_img(dst_ring, base, xe, P->storage);
-        store_img(dst_ring, base + 1, xo, P->storage);
-        if (P->storage) {
-          ye = __bfloat162float(__float2bfloat16_rn(xe));
-          yo = __bfloat162float(__float2bfloat16_rn(xo));
-        }
-      }
-      const float pe = prev[u].x, po = prev[u].y;
-      sd = fmaf(ye - pe, ye - pe, sd);
-      sd = fmaf(yo - po, yo - po, sd);
-      sx = fmaf(pe, pe, sx);
-      sx = fmaf(po, po, sx);
+      const float2 v = Y[row * ssm + pidx(n)];
+      out.put((long)(r0 + row) * W + 2 * n, v.x, -v.y, pv[u], sd, sx);
     }
   }
   // CTA sums (fixed order), then rank 0 sums the cluster's partials in rank order
-  __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     sd += __shfl_xor_sync(0xffffffffu, sd, off);
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
   }
-  if (lane == 0) { red_d[warp] = sd; red_x[warp] = sx; }
+  if (lane == 0) {
+    red_d[warp] = sd;
+    red_x[warp] = sx;
+  }
   __syncthreads();
   if (tid == 0) {
     float td = 0.f, tx = 0.f;
-    for (int w = 0; w < (nthr >> 5); ++w) { td += red_d[w]; tx += red_x[w]; }
+    for (int w = 0; w < (nthr >> 5); ++w) {
+      td += red_d[w];
+      tx += red_x[w];
+    }
     part_d = td;
     part_x = tx;
   }
@@ -561,15 +706,7 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       tsd += (double)*cl.map_shared_rank(&part_d, q);
       tsx += (double)*cl.map_shared_rank(&part_x, q);
     }
-    ProbState *st = P->st;
-    const double rel = tsx > 0.0 ? sqrt(tsd / tsx) : (tsd > 0.0 ? INFINITY : 0.0);
-    st->rel_change = rel;
-    st->calls += 1;
-    if (rel < st->tol || st->calls >= st->max_calls) {
-      st->done = 1;
-      st->converged = rel < st->tol ? 1 : 0;
-      st->final_slot = sa.dst;
-    }
+    finish_step(P->st, tsd, tsx, sa.dst);
   }
   cl.sync();   // keep shared memory alive until rank 0 has read the partials
 }
@@ -590,8 +727,16 @@ __global__ void k_spectral_constants(const float2 *__restrict__ khat, const floa
 
 }  // namespace
 
-int fft_smem_rows(int tw_cap, int buf_cap) { return (int)((2 * (size_t)tw_cap + 1 + 2 * (size_t)buf_cap) * sizeof(float2)); }
-int fft_smem_cols(int tw_cap, int buf_cap) { return (int)(((size_t)tw_cap + 2 * (size_t)buf_cap) * sizeof(float2)); }
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+
+int fft_smem_rows(int tw_cap, int buf_cap) {
+  return (int)((2 * (size_t)tw_cap + 1 + 2 * (size_t)buf_cap) * sizeof(float2));
+}
+int fft_smem_cols(int tw_cap, int buf_cap) {
+  return (int)(((size_t)tw_cap + 2 * (size_t)buf_cap) * sizeof(float2));
+}
 
 // Raises a kernel's dynamic shared-memory limit the first time a launch needs more
 // than the 48 KB default (a per-kernel high-water mark; races only repeat the call).
@@ -601,7 +746,7 @@ static cudaError_t set_smem(const void *fn, int bytes, int *high_water) {
   if (e == cudaSuccess) *high_water = bytes;
   return e;
 }
-static int hw_r2c = 0, hw_cols = 0, hw_c2r = 0;
+static int hw_r2c = 0, hw_cols = 0, hw_c2r = 0, hw_cluster = 0;
 
 cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col_buf_cap) {
   const int sr = fft_smem_rows(row_tw_cap, row_buf_cap), sc = fft_smem_cols(col_tw_cap, col_buf_cap);
@@ -648,20 +793,18 @@ cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_it
   return cudaGetLastError();
 }
 
-// Shared memory of the cluster solve for one problem (complex elements): twiddles, the
-// row band's half spectrum A, two work buffers (row band rows or column band columns).
+// Shared memory of the cluster solve for one problem (complex elements): the row band's
+// half spectrum A, and two work buffers (the band's padded rows or columns).
 void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems) {
   const int M = W / 2, Wh = M + 1;
   const int nr = (H + ncta - 1) / ncta, nc = (Wh + ncta - 1) / ncta;
   *a_elems = nr * Wh;
-  *buf_elems = std::max(nr * M, nc * (H + 1));
+  *buf_elems = std::max(nr * fft_seq_stride(M), nc * fft_seq_stride(H));
 }
 
 int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
   return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 2 * (size_t)buf_cap) * sizeof(float2));
 }
-
-static int hw_cluster = 0;
 
 cudaError_t fft_cluster_prepare(int smem, int ncta) {
   cudaError_t e = set_smem((const void *)k_fft_solve_cluster, smem, &hw_cluster);
@@ -693,7 +836,7 @@ cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, 
   return e;
 }
 
-// Largest cluster the device accepts for the cluster solve with this shared memory.
+// Number of clusters of `ncta` CTAs of the cluster solve the device can hold at once.
 int fft_cluster_max_active(int ncta, int smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ncta);

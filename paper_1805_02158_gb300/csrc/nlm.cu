@@ -6,9 +6,9 @@
 //   w(p,d) = exp(-(1/(25 h^2)) sum_{t in [-2,2]^2} (xp(p+t) - xp(p+d+t))^2),
 // xp = x extended by half-sample symmetric reflection.
 //
-// GB300 mapping. One CTA = a tile of 60 output columns x (8 * warps) output rows; the
-// tile plus a 7-pixel halo (search radius 5 + patch radius 2) is staged once in shared
-// memory, prescaled by k = sqrt(log2(e) / (25 h^2)) so that a weight is a single
+// GB300 mapping. One warp = a tile of 60 output columns x 8 output rows (warp-sized work
+// units balance evenly over the SMs; a CTA is 1-4 independent warps); the tile plus a
+// 7-pixel halo (search radius 5 + patch radius 2) is staged once in shared memory, prescaled by k = sqrt(log2(e) / (25 h^2)) so that a weight is a single
 // ex2.approx of a negated patch distance. Each lane owns 2 adjacent columns and 8 rows:
 //   * the lane's own patch rows a(rr) (12 x 2 values) stay in registers for all 121 offsets;
 //   * for each dx the lane loads the 22 candidate rows it needs for all 11 dy once, so
@@ -47,17 +47,21 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 template <int R, int MINB>
 __global__ void __launch_bounds__(128, MINB)
-k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArgs sa,
+k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_items, StepArgs sa,
       int src_is_bf16_override, float *f_override) {
-  extern __shared__ float tile[];
-  const Item it = items[blockIdx.x];
+  extern __shared__ float smem_tiles[];
+  // one independent tile of 60 x R outputs per warp (work units are warp-sized so they
+  // spread evenly over the SMs); the warp stages its own tile + 7-pixel halo
+  const int item = blockIdx.x * blockDim.y + threadIdx.y;
+  if (item >= n_items) return;
+  const Item it = items[item];
   const ProbDev *P = probs + it.prob;
   if (sa.update_state && P->st->done) return;
+  float *tile = smem_tiles + threadIdx.y * ((R + 14) * kStride);
 
   const int H = P->H, W = P->W;
   const int tr0 = it.a, tc0 = it.b;
-  const int wy = blockDim.y;
-  const int rows = R * wy + 14;
+  const int rows = R + 14;
   const float k = P->nlm_k;
 
   const void *src;
@@ -71,17 +75,16 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
           (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
   }
 
-  // Stage the tile: 8 loads in flight per thread. One reflection is exact for every pixel
+  // Stage the tile: 8 loads in flight per lane. One reflection is exact for every pixel
   // an output inside the image needs (halo 7 <= side); the clamp only keeps rows/columns
   // of partial tiles, whose outputs are not stored, inside the image.
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int nthr = 32 * wy;
+  const int tid = threadIdx.x;
   const int total = rows * kCols;
-  for (int base = tid; base < total; base += 8 * nthr) {
+  for (int base = tid; base < total; base += 8 * 32) {
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * nthr;
+      const int idx = base + u * 32;
       if (idx < total) {
         const int rr = idx / kCols;
         const int cc = idx - rr * kCols;
@@ -92,17 +95,17 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * nthr;
+      const int idx = base + u * 32;
       if (idx < total) {
         const int rr = idx / kCols;
         tile[rr * kStride + (idx - rr * kCols)] = k * v[u];
       }
     }
   }
-  __syncthreads();
+  __syncwarp();
 
   const int lane = threadIdx.x;
-  const int r0 = threadIdx.y * R;     // warp's first output row, tile-local
+  const int r0 = 0;                   // the warp's first output row, tile-local
   const int sc0 = 2 * lane + 5;       // staged column of the lane's first column
 
   // own patch rows: staged rows r0 + 5 .. r0 + R + 8 (output rows r0-2 .. r0+R+1)
@@ -181,8 +184,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, StepArg
 }  // namespace
 
 cudaError_t nlm_prepare(int wy) {
-  const int smem = (kNlmR * wy + 14) * kStride * (int)sizeof(float);
-  (void)smem;   // at most 4 warps per CTA: always under the 48 KB default
+  (void)wy;   // at most 4 warps per CTA x 8.5 KB of staged tile: under the 48 KB default
   return cudaSuccess;
 }
 
@@ -192,12 +194,13 @@ cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items,
                        StepArgs sa, int src_is_bf16, cudaStream_t s, float *f_override, int occ) {
   if (n_items <= 0) return cudaSuccess;
   if (wy < 1 || wy > 4) return cudaErrorInvalidValue;   // kernel is bounded at 128 threads
-  const size_t smem = (size_t)(kNlmR * wy + 14) * kStride * sizeof(float);
+  const size_t smem = (size_t)wy * (kNlmR + 14) * kStride * sizeof(float);
   dim3 block(32, wy);
+  const int ctas = (n_items + wy - 1) / wy;
   if (occ >= 4)
-    k_nlm<kNlmR, 4><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
+    k_nlm<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
   else
-    k_nlm<kNlmR, 3><<<n_items, block, smem, s>>>(d_probs, d_items, sa, src_is_bf16, f_override);
+    k_nlm<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
   count_launches(1);
   return cudaGetLastError();
 }
