@@ -222,7 +222,6 @@ def main():
     ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
     Ps = [red.Problem(red.config_for(p, ve="rre", ve_k=VE_K), y) for p, y in zip(problems, ys)]
     B = red.Batch(Ps)
-    B.set_phase_timing(True)
     x0s = [y.clone() for y in ys]
     outs = [torch.empty_like(y) for y in ys]
     flush = torch.empty(max(1, args.flush_mb) * 1024 * 1024 // 4, dtype=torch.float32,

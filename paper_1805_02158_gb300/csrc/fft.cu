@@ -201,8 +201,10 @@ __device__ __forceinline__ int pick_radix(int rem) {
 }
 
 // Forward FFT of nseq padded sequences of length n (2^a 3^b) held at x + s * ss; ping-pongs
-// between x and y and returns the buffer holding the result. Ends with a barrier.
-__device__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, int ss,
+// between x and y and returns the buffer holding the result. Ends with a barrier. Not
+// inlined: one copy of the unrolled radix passes serves every call site (instruction
+// cache).
+__device__ __noinline__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, int ss,
                             const float2 *__restrict__ tw, int tid, int nthr) {
   float2 *in = x, *out = y;
   int Ns = 1, rem = n;
