@@ -185,6 +185,65 @@ def ve_vs_fp_study(problems, Ps, torch, red):
             "rre_calls_to_fp200_cost_mean": float(np.mean(fill(need_cost)))}
 
 
+SERVE_RATE_HZ = 200.0
+SERVE_TOL = 1e-4
+SERVE_CAP = 300
+
+
+def _serving_input(seed):
+    """One request of the serving stream as plain data (runs in a spawned worker)."""
+    from paper_1805_02158_gb300 import synth
+    p = synth.serving_request(seed)
+    return {"task": p.task, "height": p.height, "width": p.width, "scale": p.scale,
+            "psf": p.psf, "sigma": p.sigma, "alpha": p.alpha, "nlm_h": p.nlm_h,
+            "y": np.ascontiguousarray(p.y.astype(np.float32))}
+
+
+def serving_leg(red, n_req, budget_gb=32, slots=32):
+    """Poisson arrivals (200 req/s) of mixed deblurring / x3 SR requests, sides 128-1024,
+    rel-change tolerance 1e-4, cap 300 FP calls, through the serving loop; latency is
+    submission to completion (host result written). RRE k = 5, then plain FP on the same
+    stream for comparison."""
+    import multiprocessing as mp
+    from paper_1805_02158_gb300 import synth
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        reqs = pool.map(_serving_input, range(n_req))
+    arrivals = synth.poisson_arrivals(SERVE_RATE_HZ, n_req, seed=0)
+    out = {"requests": n_req, "rate_hz": SERVE_RATE_HZ, "tol": SERVE_TOL, "cap_fp_calls": SERVE_CAP,
+           "slots": slots, "budget_gb": budget_gb,
+           "mix": {"deblur": sum(r["task"] == "deblur" for r in reqs),
+                   "sr": sum(r["task"] == "sr" for r in reqs)}}
+    for ve in ("rre", "none"):
+        S = red.Server(budget_gb << 30, slots)
+        outs = [np.zeros((r["height"], r["width"]), np.float32) for r in reqs]
+        cfgs = [red.make_config(task=r["task"], height=r["height"], width=r["width"],
+                                scale=r["scale"], psf=r["psf"], sigma=r["sigma"], alpha=r["alpha"],
+                                nlm_h=r["nlm_h"], ve=ve, ve_k=VE_K) for r in reqs]
+        tickets = []
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(S.submit(cfgs[i], r["y"], outs[i], SERVE_CAP, SERVE_TOL))
+        stats = []
+        for t in tickets:
+            st, s = S.wait(t, -1)
+            stats.append(s)
+        wall = time.perf_counter() - t0
+        S.close()
+        lat = np.array([s["ms_total"] for s in stats])
+        calls = np.array([s["fp_calls"] for s in stats])
+        pix = np.array([r["height"] * r["width"] for r in reqs])
+        out["rre" if ve == "rre" else "plain_fp"] = {
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": n_req / wall, "mpix_iter_per_s": float((pix * calls).sum()) / wall / 1e6,
+            "fp_calls_mean": float(calls.mean()),
+            "converged_frac": float(np.mean([s["converged"] for s in stats])), "wall_s": wall}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +254,8 @@ def main():
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer (0: none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving leg (0: skip it)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,6 +405,9 @@ def main():
     study = None
     if not args.no_study and rank == 0:
         study = ve_vs_fp_study(problems, Ps, torch, red)
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        serving = serving_leg(red, args.serve_requests)
 
     if rank != 0:
         if dist:
@@ -371,6 +435,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ve_vs_fp": study,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -86,7 +86,7 @@ static Layout layout_for(const red_config &c, int nslots, int slot_stride) {
   L.kh = sr ? 0 : cv.take((size_t)c.height * Wh * 8);
   L.cc = sr ? 0 : cv.take((size_t)c.height * Wh * 8);
   L.gg = sr ? 0 : cv.take((size_t)c.height * Wh * 4);
-  L.row_stats = cv.take((size_t)c.height * 8);
+  L.row_stats = cv.take((size_t)std::max(c.height, 32) * 8);   // rows, or cluster CTAs
   L.gram = cv.take(nchunks * kMaxPairs * 8);
   L.coef = cv.take(kMaxK * 8);
   L.gamma = cv.take(kMaxK * 8);

@@ -522,22 +522,23 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
 //   cluster barrier; each CTA gathers its band of spectrum columns from every CTA's A
 //   through distributed shared memory, column FFT, X = C + G F, inverse column FFT
 //   cluster barrier; each CTA scatters its columns back into the owners' A
-//   cluster barrier; rows C2R of the band -> x_{k+1}, statistics, termination test.
+//   cluster barrier; rows C2R of the band -> x_{k+1}, statistics; the last CTA to finish
+//   sums the per-CTA statistics and runs the termination test.
 // Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
 // x_{k+1} (4 B); the spectrum never leaves the chip.
-constexpr int kClusterThreads = 512;
+constexpr int kClusterThreads = 256;   // two CTAs per SM fit, so 16-CTA clusters co-reside
 
 __device__ __forceinline__ int band_lo(int q, int n, const FastDiv &by_ncta) { return by_ncta.div(q * n); }
 __device__ __forceinline__ int band_owner(int h, int ncta, const FastDiv &by_n) {
   return by_n.div((h + 1) * ncta - 1);
 }
 
-__global__ void __launch_bounds__(kClusterThreads)
+__global__ void __launch_bounds__(kClusterThreads, 2)
 k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ list, StepArgs sa,
                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
   extern __shared__ float2 sm[];
-  __shared__ float part_d, part_x;
   __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
+  __shared__ int is_last;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
@@ -555,9 +556,6 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   float2 *X0 = A + a_cap;
   float2 *X1 = X0 + buf_cap;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
-  for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
-  for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   const FastDiv fdm(M), fdwh(Wh), fdc(nc > 0 ? nc : 1);
   // x_k for the statistics, fetched first (its latency hides behind the transforms)
   constexpr int kPrev = 4;
@@ -573,17 +571,29 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       prev[u] = out.prev((long)(r0 + row) * W + 2 * n);
     }
   }
-  // 1. rows of f, real to half spectrum
-  copy_batched<4>(nr * M, tid, nthr,
+  // twiddle tables and the band's rows of f, all loads in flight together
+  const int ntw = M + (M + 1) + H;
+  copy_batched<8>(ntw + nr * M, tid, nthr,
       [&](int idx) {
+        if (idx < M) return P->tw_m[idx];
+        if (idx < 2 * M + 1) return P->tw_w[idx - M];
+        if (idx < ntw) return P->tw_h[idx - 2 * M - 1];
         int row, n;
-        fdm.divmod(idx, row, n);
+        fdm.divmod(idx - ntw, row, n);
         return reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
       },
       [&](int idx, float2 v) {
-        int row, n;
-        fdm.divmod(idx, row, n);
-        X0[row * ssm + pidx(n)] = v;
+        if (idx < M) {
+          twm[idx] = v;
+        } else if (idx < 2 * M + 1) {
+          tww[idx - M] = v;
+        } else if (idx < ntw) {
+          twh[idx - 2 * M - 1] = v;
+        } else {
+          int row, n;
+          fdm.divmod(idx - ntw, row, n);
+          X0[row * ssm + pidx(n)] = v;
+        }
       });
   __syncthreads();
   const float2 *Z = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
@@ -692,25 +702,32 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     red_x[warp] = sx;
   }
   __syncthreads();
+  if (!sa.update_state) return;   // no distributed shared memory is used past barrier 3
+  // per-CTA partials through global memory; the last CTA of the cluster to arrive sums
+  // them in rank order (fixed order, no extra cluster barriers)
   if (tid == 0) {
     float td = 0.f, tx = 0.f;
     for (int w = 0; w < (nthr >> 5); ++w) {
       td += red_d[w];
       tx += red_x[w];
     }
-    part_d = td;
-    part_x = tx;
+    P->row_stats[rank] = make_float2(td, tx);
+    __threadfence();
+    is_last = atomicAdd(&P->st->counter, 1u) == (unsigned)(ncta - 1);
   }
-  cl.sync();
-  if (sa.update_state && rank == 0 && tid == 0) {
+  __syncthreads();
+  if (tid == 0 && is_last) {
+    __threadfence();
     double tsd = 0.0, tsx = 0.0;
     for (int q = 0; q < ncta; ++q) {
-      tsd += (double)*cl.map_shared_rank(&part_d, q);
-      tsx += (double)*cl.map_shared_rank(&part_x, q);
+      const float2 v = __ldcg(&P->row_stats[q]);
+      tsd += (double)v.x;
+      tsx += (double)v.y;
     }
     finish_step(P->st, tsd, tsx, sa.dst);
+    P->st->counter = 0;
+    __threadfence();
   }
-  cl.sync();   // keep shared memory alive until rank 0 has read the partials
 }
 
 __global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,

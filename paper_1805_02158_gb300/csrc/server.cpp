@@ -56,7 +56,7 @@ struct Request {
   bool finished = false;
   red_stats stats{};
   Clock::time_point t_submit, t_admit, t_done;
-  red_problem_s *prob = nullptr;
+  red_problem_s *prob = nullptr;   // set at admission: a pooled problem, or null (create)
 };
 
 std::string key_of(const red_config &c, const std::vector<float> &psf) {
@@ -99,14 +99,18 @@ struct red_server_s {
   std::map<std::string, std::vector<red_problem_s *>> pool;
   std::map<std::string, size_t> pool_bytes;
   std::vector<std::shared_ptr<Request>> running;
+  struct Group {                                         // launch tables of one group
+    std::vector<red_problem_s *> members;                // as of the last build
+    red::Plan plan;
+    red::ProbDev *d_pds = nullptr;
+    int pds_cap = 0;
+  };
+  std::map<std::string, std::unique_ptr<Group>> groups;
   float *d_stage = nullptr;                              // y / x0 staging (largest image)
   size_t stage_elems = 0;
   ProbState *h_states = nullptr;
   ProbState *d_states = nullptr;
   int states_cap = 0;
-  red::Plan plan;
-  red::ProbDev *d_pds = nullptr;
-  int pds_cap = 0;
   std::string sticky_error;
 };
 
@@ -143,6 +147,11 @@ bool make_room(red_server_s *S, size_t need) {
     red_problem_s *p = S->pool[best].back();
     S->pool[best].pop_back();
     S->used -= bb;
+    // a group whose last build included p must rebuild (its address may be reused)
+    for (auto &kv : S->groups)
+      if (std::find(kv.second->members.begin(), kv.second->members.end(), p) !=
+          kv.second->members.end())
+        kv.second->members.clear();
     delete p;
   }
   return true;
@@ -156,22 +165,21 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   const int lw = r->cfg.task == RED_SR ? W / r->cfg.scale : W;
   ensure_stage(S, (size_t)H * W);
   CUDA_OK(cudaMemcpyAsync(S->d_stage, r->y.data(), (size_t)lh * lw * 4, cudaMemcpyHostToDevice, s));
-  red_problem_s *P = nullptr;
-  auto &vec = S->pool[r->key];
-  if (!vec.empty()) {
-    P = vec.back();
-    vec.pop_back();
+  red_problem_s *P = r->prob;
+  if (P) {
     red_status st = red_set_observation(P, S->d_stage, 0, s);
     if (st != RED_OK) throw Fail{st, red_last_error()};
   } else {
+    // the bytes were reserved (S->used) when the request was admitted
     red_config c = r->cfg;
     c.psf = r->psf.data();
     red_problem out = nullptr;
     red_status st = red_create_problem(&c, S->d_stage, s, &out);
-    if (st != RED_OK) throw Fail{st, red_last_error()};
+    if (st != RED_OK) {
+      S->used -= r->footprint;
+      throw Fail{st, red_last_error()};
+    }
     P = out;
-    S->used += r->footprint;
-    S->pool_bytes[r->key] = r->footprint;
   }
   r->prob = P;
   // x0 = y for deblurring; pixel replication of y, edge-extended, for SR
@@ -205,39 +213,49 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   r->t_admit = Clock::now();
 }
 
-// One cycle of Algorithm 3 for the running requests of one group.
-void run_group_cycle(red_server_s *S, const std::vector<red_problem_s *> &members, int ve, int k,
-                     int m) {
+// One cycle of Algorithm 3 for the running requests of one group. The work lists and
+// descriptor table are rebuilt only when the group's membership changed.
+void run_group_cycle(red_server_s *S, red_server_s::Group &g,
+                     const std::vector<red_problem_s *> &members, int ve, int k, int m) {
   cudaStream_t s = S->stream;
   const int n = (int)members.size();
-  std::vector<ProbDev> pds;
-  for (auto *p : members) pds.push_back(p->pd);   // st = the problem's own state
-  LaunchCfg lc;
-  S->plan.build(pds, lc);
-  for (int i = 0; i < n; ++i) pds[i].n_row_items = S->plan.n_row_items[i];
-  if (n > S->pds_cap) {
-    if (S->d_pds) cudaFree(S->d_pds);
-    S->d_pds = nullptr;
-    CUDA_OK(cudaMalloc(&S->d_pds, sizeof(ProbDev) * n));
-    S->pds_cap = n;
+  if (members != g.members) {
+    std::vector<ProbDev> pds;
+    for (auto *p : members) pds.push_back(p->pd);   // st = the problem's own state
+    LaunchCfg lc;
+    g.plan.build(pds, lc);
+    for (int i = 0; i < n; ++i) pds[i].n_row_items = g.plan.n_row_items[i];
+    if (n > g.pds_cap) {
+      if (g.d_pds) cudaFree(g.d_pds);
+      g.d_pds = nullptr;
+      CUDA_OK(cudaMalloc(&g.d_pds, sizeof(ProbDev) * n));
+      g.pds_cap = n;
+    }
+    CUDA_OK(cudaMemcpy(g.d_pds, pds.data(), sizeof(ProbDev) * n, cudaMemcpyHostToDevice));
+    prepare_launch_attrs(g.plan);
+    g.members = members;
   }
-  CUDA_OK(cudaMemcpyAsync(S->d_pds, pds.data(), sizeof(ProbDev) * n, cudaMemcpyHostToDevice, s));
-  prepare_launch_attrs(S->plan);
   for (const CycleOp &op : cycle_ops(ve, k, m)) {
     if (op.kind == 0) {
       StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
-      launch_fp_step(S->d_pds, S->plan, sa, 0, s);
+      launch_fp_step(g.d_pds, g.plan, sa, 0, s);
     } else {
       VeArgs va{};
       for (size_t i = 0; i < op.slots.size(); ++i) va.slots[i] = op.slots[i];
       va.nvec = (int)op.slots.size();
       va.out_slot = op.out;
       va.update_state = 1;
-      launch_ve(S->d_pds, n, S->plan, va, s);
+      launch_ve(g.d_pds, n, g.plan, va, s);
     }
   }
-  // the host copy of pds is read by the async copy above
-  CUDA_OK(cudaStreamSynchronize(s));
+}
+
+void release_group(red_server_s::Group &g) {
+  g.plan.release();
+  if (g.d_pds) cudaFree(g.d_pds);
+  g.d_pds = nullptr;
+  g.pds_cap = 0;
+  g.members.clear();
 }
 
 void scheduler(red_server_s *S) {
@@ -260,11 +278,20 @@ void scheduler(red_server_s *S) {
         S->cv_done.notify_all();
       }
       // FIFO admission by slots and device footprint
+      // (an idle problem of the same key is taken now, so that make_room cannot free it
+      // for a later request; a new problem's bytes are reserved now)
       while (!S->waiting.empty() &&
              (int)(S->running.size() + to_admit.size()) < S->max_slots) {
         auto r = S->waiting.front();
-        const bool pooled = !S->pool[r->key].empty();
-        if (!pooled && !make_room(S, r->footprint)) break;
+        auto &idle = S->pool[r->key];
+        if (!idle.empty()) {
+          r->prob = idle.back();
+          idle.pop_back();
+        } else {
+          if (!make_room(S, r->footprint)) break;
+          S->used += r->footprint;
+          S->pool_bytes[r->key] = r->footprint;
+        }
         S->waiting.pop_front();
         to_admit.push_back(r);
       }
@@ -274,6 +301,11 @@ void scheduler(red_server_s *S) {
         admit(S, r);
         S->running.push_back(r);
       } catch (const Fail &e) {
+        if (r->prob) {   // a pooled problem whose observation upload failed
+          S->used -= S->pool_bytes[r->key];
+          delete r->prob;
+          r->prob = nullptr;
+        }
         r->stats = red_stats{};
         finish(S, r, e.st);
       }
@@ -288,7 +320,9 @@ void scheduler(red_server_s *S) {
       }
       for (auto &kv : groups) {
         const red_config *c = gcfg[kv.first];
-        run_group_cycle(S, kv.second, c->ve, c->ve_k, c->ve_m);
+        auto &g = S->groups[kv.first];
+        if (!g) g.reset(new red_server_s::Group());
+        run_group_cycle(S, *g, kv.second, c->ve, c->ve_k, c->ve_m);
       }
       // termination states
       const int n = (int)S->running.size();
@@ -344,6 +378,7 @@ void scheduler(red_server_s *S) {
       for (auto &kv : S->pool)
         for (auto *p : kv.second) delete p;
       S->pool.clear();
+      for (auto &kv : S->groups) release_group(*kv.second);
     }
   }
 }
@@ -446,8 +481,7 @@ red_status red_server_destroy(red_server s) {
     if (s->th.joinable()) s->th.join();
     for (auto &kv : s->pool)
       for (auto *p : kv.second) delete p;
-    s->plan.release();
-    if (s->d_pds) cudaFree(s->d_pds);
+    for (auto &kv : s->groups) release_group(*kv.second);
     if (s->d_stage) cudaFree(s->d_stage);
     if (s->h_states) cudaFreeHost(s->h_states);
     if (s->stream) cudaStreamDestroy(s->stream);

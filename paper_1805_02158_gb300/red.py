@@ -322,3 +322,61 @@ class Batch:
                                                _stream_ptr(stream)), "red_batch_solve_host",
                     ok=(RED_OK, RED_ENOT_CONVERGED))
         return [s.as_dict() for s in stats]
+
+
+class Server:
+    """A red_server: requests (config + host observation) solved by a scheduler thread
+    with continuous batching. Host buffers of pending requests are kept referenced."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        h = ctypes.c_void_p()
+        _check(lib().red_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
+               "red_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, cfg, y_host, x_out_host, max_fp_calls, rel_tol=0.0):
+        """y_host / x_out_host: C-contiguous float32 numpy arrays. Returns the ticket."""
+        import numpy as np
+        for a in (y_host, x_out_host):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+                raise TypeError("expected C-contiguous float32 numpy arrays")
+        t = ctypes.c_uint64()
+        _check(lib().red_submit(self.handle, ctypes.byref(cfg), ctypes.c_void_p(y_host.ctypes.data),
+                                ctypes.c_void_p(x_out_host.ctypes.data), int(max_fp_calls),
+                                float(rel_tol), ctypes.byref(t)), "red_submit")
+        self._keep[t.value] = (cfg, y_host, x_out_host)
+        return t.value
+
+    def poll(self, ticket):
+        """(status, stats dict or None while RED_EBUSY)."""
+        s = Stats()
+        st = lib().red_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(s))
+        if st == RED_EBUSY:
+            return st, None
+        if st == RED_EINVAL:
+            _check(st, "red_poll")
+        return st, s.as_dict()
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(status, stats dict or None on RED_ETIMEOUT)."""
+        s = Stats()
+        st = lib().red_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(s))
+        if st == RED_ETIMEOUT:
+            return st, None
+        if st == RED_EINVAL:
+            _check(st, "red_wait")
+        self._keep.pop(ticket, None)
+        return st, s.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib().red_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -132,6 +132,28 @@ def circular_blur_direct(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
     return out
 
 
+def gaussian_taps(k: int, s: float) -> np.ndarray:
+    """1-D factor of gaussian_psf: gaussian_psf(k, s) = outer(t, t) with t = these taps."""
+    r = (k - 1) / 2.0
+    a = np.arange(k, dtype=np.float64) - r
+    g = np.exp(-(a ** 2) / (2.0 * s * s))
+    return g / g.sum()
+
+
+def circular_blur_separable(x: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Circular convolution with the PSF outer(u, v) (centre ((K1-1)/2, (K2-1)/2)), as a
+    column pass then a row pass of taps: the same result as circular_blur_direct with that
+    PSF up to rounding, with K1 + K2 instead of K1 K2 passes (used for large images)."""
+    c1, c2 = (len(u) - 1) // 2, (len(v) - 1) // 2
+    t = np.zeros_like(x, dtype=np.float64)
+    for a in range(len(u)):
+        t += u[a] * np.roll(x, shift=a - c1, axis=0)
+    out = np.zeros_like(x, dtype=np.float64)
+    for b in range(len(v)):
+        out += v[b] * np.roll(t, shift=b - c2, axis=1)
+    return out
+
+
 def lr_shape(height: int, width: int, scale: int):
     return height // scale, width // scale
 
@@ -179,20 +201,23 @@ def upsample_replicate(z: np.ndarray, scale: int, height: int, width: int) -> np
 
 
 def make_deblur(seed: int, height: int, width: int, psf: np.ndarray, sigma: float,
-                alpha: float = 0.02) -> Problem:
+                alpha: float = 0.02, blur=None) -> Problem:
+    """blur: optional callable x -> H x (default: circular_blur_direct with psf)."""
     x = ellipse_image(seed, height, width)
     n = Stream(seed, TAG_NOISE).normal(height * width).reshape(height, width)
-    y = circular_blur_direct(x, psf) + sigma * n
+    hx = blur(x) if blur is not None else circular_blur_direct(x, psf)
+    y = hx + sigma * n
     return Problem(seed=seed, task="deblur", height=height, width=width, scale=1, psf=psf,
                    sigma=sigma, alpha=alpha, x_true=x, y=y, x0=y.copy())
 
 
 def make_sr(seed: int, height: int, width: int, psf: np.ndarray, scale: int, sigma: float,
-            alpha: float = 0.02) -> Problem:
+            alpha: float = 0.02, blur=None) -> Problem:
     x = ellipse_image(seed, height, width)
     h, w = lr_shape(height, width, scale)
     n = Stream(seed, TAG_NOISE).normal(h * w).reshape(h, w)
-    y = circular_blur_direct(x, psf)[: scale * h: scale, : scale * w: scale] + sigma * n
+    hx = blur(x) if blur is not None else circular_blur_direct(x, psf)
+    y = hx[: scale * h: scale, : scale * w: scale] + sigma * n
     x0 = upsample_replicate(y, scale, height, width)
     return Problem(seed=seed, task="sr", height=height, width=width, scale=scale, psf=psf,
                    sigma=sigma, alpha=alpha, x_true=x, y=y, x0=x0)
@@ -243,12 +268,16 @@ SERVE_SIDES = (128, 192, 256, 384, 512, 768, 1024)
 def serving_request(seed: int) -> Problem:
     """One request of the serving stream: 70% deblurring (Gaussian 25x25 std 1.6,
     sigma sqrt 2), 30% x3 super-resolution (Sec. IV-B physics); side drawn from
-    {128,...,1024}."""
+    {128,...,1024}. The Gaussian blur is applied as two 1-D passes (large sides)."""
     s = Stream(seed, TAG_PROBLEM)
     side = s.choice(SERVE_SIDES)
     if s.uniform1() < 0.7:
-        return deblur_gauss256(seed, side)
-    return sr_x3(seed, side)
+        t = gaussian_taps(25, 1.6)
+        return make_deblur(seed, side, side, gaussian_psf(25, 1.6), math.sqrt(2.0),
+                           blur=lambda x: circular_blur_separable(x, t, t))
+    t = gaussian_taps(7, 1.6)
+    return make_sr(seed, side, side, gaussian_psf(7, 1.6), 3, 5.0,
+                   blur=lambda x: circular_blur_separable(x, t, t))
 
 
 def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
