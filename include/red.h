@@ -130,6 +130,31 @@ red_status red_denoise(red_problem p, const void *x_dev, void *f_dev, void *stre
 red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_vec,
                               void *x_out_dev, double *gamma_host, void *stream);
 
+/* Allocation-free extrapolation. The paper has no counterpart: this is the extrapolation
+ * of red_ve_extrapolate for a caller that holds iterates of its own fixed-point
+ * iteration and cannot allocate device memory at the call site: cudaMalloc and cudaFree
+ * synchronise the whole device (stalling every other stream of a serving process), and a
+ * process whose device memory is reserved up front by another allocator has no room for
+ * a problem's buffers. No problem handle is needed and nothing is allocated: the Gram
+ * partial sums, xi, gamma and the status live in one file-scope device array of
+ * 1 MiB + 384 bytes per device (1024 rows of 136 partial sums, enough for any n).
+ *   xs_dev:  host array of n_vec device pointers to float32 vectors x_m .. x_{m+kappa+1},
+ *            each of n elements, 3 <= n_vec <= 17 (any alignment; 16-byte aligned
+ *            vectors take the vectorised path).
+ *   n:       elements per vector, 1 <= n <= 2^31 - 1; larger n returns RED_EINVAL.
+ *   method:  RED_VE_MPE (Algorithm 1) or RED_VE_RRE (Eq. (19)).
+ *   x_out_dev: device float32, n elements, may alias xs_dev[0]; on RED_EVE_BREAKDOWN it
+ *            holds the last iterate.
+ *   gamma_host: null, or room for kappa + 1 doubles.
+ * The first call on each device looks up the array's address (with that device current)
+ * and should come before any stream capture. The call zeroes the status block, launches
+ * three kernels on `stream` and synchronises it. All calls on one device share the one
+ * array: calls that overlap in time (other streams or host threads) race and must be
+ * serialised by the caller. Errors: RED_EINVAL (arguments, size), RED_ECUDA. */
+red_status red_ve_extrapolate_static(const void *const *xs_dev, int n_vec, int64_t n,
+                                     int method, void *x_out_dev, double *gamma_host,
+                                     void *stream);
+
 /* Full solve, Algorithm 3: cycles of ve_m + ve_k FP steps followed by one extrapolation
  * (plain FP iteration when ve = RED_VE_NONE), until the relative change of an FP step is
  * below rel_tol or max_fp_calls FP steps were made; x_out is that last FP iterate.

@@ -19,7 +19,13 @@
 //                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
 // Chunks are fixed per problem, so the reduction order (and the result) does not depend
 // on the launch shape or on other problems in the batch.
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
+#include "runtime.h"
 
 namespace red {
 
@@ -516,4 +522,248 @@ cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n
   return cudaGetLastError();
 }
 
+// ---- allocation-free extrapolation ------------------------------------------------------
+// The same three steps over plain device vectors, with every scratch word (Gram partial
+// sums, xi, gamma, status) in one file-scope device array instead of a problem's buffers.
+namespace {
+
+constexpr int kStaticGramCtas = 1024;                      // Gram partial rows (max)
+constexpr int kStaticPartials = kStaticGramCtas * kMaxPairs;
+constexpr int kStaticStateDoubles = 16;
+constexpr int kStaticDoubles = kStaticPartials + 2 * kMaxK + kStaticStateDoubles;
+static_assert(sizeof(ProbState) <= kStaticStateDoubles * sizeof(double), "state block");
+
+// 1,114,112 + 384 bytes: per-CTA Gram partials | xi | gamma | ProbState
+static __device__ __align__(256) double g_ve_scratch[kStaticDoubles];
+
+struct StaticVe {
+  const float *x[kMaxK + 1];
+  float *out;
+  long n;
+  int n_chunks;       // kGramChunk-pixel chunks of the vectors
+  double *part;       // gridDim.x (Gram launch) rows of kMaxPairs
+  int n_part;
+  int method;
+  double *coef, *gamma;
+  ProbState *st;
+};
+
+// Gram partials: CTA b accumulates chunks b, b + gridDim.x, ... (double-float, exact
+// products as in k_gram) and writes one row of partial sums.
+template <int K>
+__global__ void __launch_bounds__(128) k_gram_static(StaticVe a) {
+  constexpr int NP = K * (K + 1) / 2;
+  __shared__ double red[4][NP];
+  GramAcc<K> acc;
+  acc.zero();
+  const int tid = threadIdx.x;
+  bool aligned = true;
+#pragma unroll
+  for (int i = 0; i <= K; ++i) aligned = aligned && ((reinterpret_cast<uintptr_t>(a.x[i]) & 15) == 0);
+  for (long c = blockIdx.x; c < a.n_chunks; c += gridDim.x) {
+    const long begin = c * kGramChunk;
+    const long end = min(a.n, begin + kGramChunk);
+    long p0 = begin;
+    if (aligned) {   // begin is a multiple of 4
+      const int nv = (int)((end - begin) >> 2);
+      for (int v = tid; v < nv; v += blockDim.x) {
+        float4 q[K + 1];
+#pragma unroll
+        for (int i = 0; i <= K; ++i) q[i] = __ldcs(reinterpret_cast<const float4 *>(a.x[i] + begin) + v);
+        float x[K + 1];
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].x;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].y;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].z;
+        acc.add(x);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) x[i] = q[i].w;
+        acc.add(x);
+      }
+      p0 = begin + ((long)nv << 2);
+    }
+    for (long p = p0 + tid; p < end; p += blockDim.x) {
+      float x[K + 1];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) x[i] = a.x[i][p];
+      acc.add(x);
+    }
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    float h = acc.hi[q], l = acc.lo[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+      const float s = __fadd_rn(h, h2);
+      const float z = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
+      h = s;
+      l = __fadd_rn(__fadd_rn(l, l2), e);
+    }
+    if (lane == 0) red[warp][q] = (double)h + (double)l;
+  }
+  __syncthreads();
+  if (tid < NP) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][tid];
+    a.part[(size_t)blockIdx.x * kMaxPairs + tid] = v;
+  }
+}
+
+// The FP64 solve of ve_solve_k on a descriptor that points into the static scratch.
+template <int K>
+__global__ void __launch_bounds__(32) k_ve_solve_static(StaticVe a) {
+  ProbDev P{};
+  P.n_chunks = a.n_part;
+  P.gram_part = a.part;
+  P.ve_method = a.method;
+  P.ve_coef = a.coef;
+  P.gamma = a.gamma;
+  P.st = a.st;
+  ve_solve_k<K>(&P, 0);
+}
+
+// x_(m,kappa) = x_m + sum_j xi_j (x_{m+j+1} - x_{m+j}); the last iterate on breakdown.
+template <int K>
+__global__ void __launch_bounds__(256) k_combine_static(StaticVe a) {
+  constexpr int kap = K - 1;
+  const int brk = a.st->ve_status;
+  float xi[kap > 0 ? kap : 1];
+#pragma unroll
+  for (int j = 0; j < kap; ++j) xi[j] = (float)a.coef[j];
+  bool vec = (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
+#pragma unroll
+  for (int i = 0; i <= K; ++i) vec = vec && ((reinterpret_cast<uintptr_t>(a.x[i]) & 15) == 0);
+  const long stride = (long)gridDim.x * blockDim.x;
+  long p0 = 0;
+  if (vec) {
+    const long nv = a.n >> 2;
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nv; v += stride) {
+      float4 r;
+      if (brk) {
+        r = reinterpret_cast<const float4 *>(a.x[K])[v];
+      } else {
+        float4 x[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) x[i] = __ldcs(reinterpret_cast<const float4 *>(a.x[i]) + v);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kap; ++j) {
+          s.x = fmaf(xi[j], x[j + 1].x - x[j].x, s.x);
+          s.y = fmaf(xi[j], x[j + 1].y - x[j].y, s.y);
+          s.z = fmaf(xi[j], x[j + 1].z - x[j].z, s.z);
+          s.w = fmaf(xi[j], x[j + 1].w - x[j].w, s.w);
+        }
+        r = make_float4(x[0].x + s.x, x[0].y + s.y, x[0].z + s.z, x[0].w + s.w);
+      }
+      reinterpret_cast<float4 *>(a.out)[v] = r;
+    }
+    p0 = nv << 2;
+  }
+  for (long p = p0 + blockIdx.x * (long)blockDim.x + threadIdx.x; p < a.n; p += stride) {
+    float val;
+    if (brk) {
+      val = a.x[K][p];
+    } else {
+      float prev = a.x[0][p];
+      const float x0 = prev;
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < kap; ++j) {
+        const float nx = a.x[j + 1][p];
+        s = fmaf(xi[j], nx - prev, s);
+        prev = nx;
+      }
+      val = x0 + s;
+    }
+    a.out[p] = val;
+  }
+}
+
+// Device address of g_ve_scratch, looked up once per device with that device current.
+std::mutex g_static_mu;
+std::vector<double *> g_static_addr;
+
+double *static_scratch(int dev) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+  if (!g_static_addr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ve_scratch);
+    if (e != cudaSuccess)
+      throw Fail{RED_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+    g_static_addr[dev] = static_cast<double *>(ptr);
+  }
+  return g_static_addr[dev];
+}
+
+}  // namespace
 }  // namespace red
+
+using namespace red;
+
+extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n_vec, int64_t n,
+                                                int method, void *x_out_dev, double *gamma_host,
+                                                void *stream) {
+  return guarded([&] {
+    CHECK_ARG(xs_dev && x_out_dev, "null argument");
+    CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 17]");
+    CHECK_ARG(method == RED_VE_MPE || method == RED_VE_RRE, "method must be RED_VE_MPE or RED_VE_RRE");
+    CHECK_ARG(n >= 1, "n must be positive");
+    const int64_t max_n = 2147483647;   // chunk counts and launch sizes are 32-bit
+    if (n > max_n)
+      throw Fail{RED_EINVAL, "n = " + std::to_string(n) + " exceeds the limit of " +
+                                 std::to_string(max_n) + " elements per vector"};
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    double *scratch = static_scratch(dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StaticVe a{};
+    for (int i = 0; i < n_vec; ++i) {
+      CHECK_ARG(xs_dev[i] != nullptr, "null vector");
+      a.x[i] = static_cast<const float *>(xs_dev[i]);
+    }
+    a.out = static_cast<float *>(x_out_dev);
+    a.n = n;
+    a.n_chunks = (int)((n + kGramChunk - 1) / kGramChunk);
+    a.n_part = std::min(a.n_chunks, kStaticGramCtas);
+    a.part = scratch;
+    a.method = method;
+    a.coef = scratch + kStaticPartials;
+    a.gamma = a.coef + kMaxK;
+    a.st = reinterpret_cast<ProbState *>(a.gamma + kMaxK);
+    // the state block starts at zero; every partial, xi and gamma read is written first
+    CUDA_OK(cudaMemsetAsync(a.st, 0, sizeof(ProbState), s));
+    const int K = n_vec - 1;
+    const int comb_ctas = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 4 * 152);
+    switch (K) {
+#define RED_STATIC_CASE(k)                                      \
+  case k:                                                       \
+    k_gram_static<k><<<a.n_part, 128, 0, s>>>(a);               \
+    k_ve_solve_static<k><<<1, 32, 0, s>>>(a);                   \
+    k_combine_static<k><<<comb_ctas, 256, 0, s>>>(a);           \
+    break;
+      RED_K_CASES(RED_STATIC_CASE)
+#undef RED_STATIC_CASE
+      default: throw Fail{RED_EINVAL, "n_vec must be in [3, 17]"};
+    }
+    count_launches(3);
+    CUDA_OK(cudaGetLastError());
+    double hg[kMaxK];
+    ProbState hs;
+    CUDA_OK(cudaMemcpyAsync(hg, a.gamma, kMaxK * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(&hs, a.st, sizeof(ProbState), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    if (hs.ve_status) return RED_EVE_BREAKDOWN;
+    if (gamma_host)
+      for (int i = 0; i < K; ++i) gamma_host[i] = hg[i];
+    return RED_OK;
+  });
+}

@@ -72,6 +72,9 @@ _SIGS = {
     "red_denoise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "red_ve_extrapolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "red_ve_extrapolate_static": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "red_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_void_p]),
     "red_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -186,6 +189,25 @@ def footprint(cfg: Config) -> int:
     out = ctypes.c_size_t()
     _check(lib().red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out)), "red_problem_footprint")
     return int(out.value)
+
+
+def ve_extrapolate_static(xs, x_out, method="rre", stream=None):
+    """red_ve_extrapolate_static: extrapolates device float32 vectors xs (x_m .. x_{m+kappa+1},
+    same number of elements) into x_out without a problem handle and without allocating.
+    Returns (status, gamma), gamma None on breakdown."""
+    n = xs[0].numel()
+    for t in list(xs) + [x_out]:
+        if t.numel() != n:
+            raise ValueError("all vectors must have the same number of elements")
+    arr = (ctypes.c_void_p * len(xs))(*[_dptr(x).value for x in xs])
+    gam = (ctypes.c_double * 16)()
+    m = VE_NAMES[method]
+    st = _check(lib().red_ve_extrapolate_static(arr, len(xs), n, m, _dptr(x_out), gam,
+                                                _stream_ptr(stream)),
+                "red_ve_extrapolate_static", ok=(RED_OK, RED_EVE_BREAKDOWN))
+    if st == RED_EVE_BREAKDOWN:
+        return st, None
+    return st, [gam[i] for i in range(len(xs) - 1)]
 
 
 class Problem:
