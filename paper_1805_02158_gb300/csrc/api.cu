@@ -166,6 +166,13 @@ int fft_cluster_override() {
   return (e && *e) ? std::atoi(e) : -1;
 }
 
+// RED_SR_CLUSTER=<n> forces the cluster size of the super-resolution CG solve (8 or 16).
+int sr_cluster_override() {
+  const char *e = std::getenv("RED_SR_CLUSTER");
+  const int v = (e && *e) ? std::atoi(e) : -1;
+  return (v == 8 || v == 16) ? v : -1;
+}
+
 void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
   release();
   lc = cfg;
@@ -233,6 +240,43 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
     CUDA_OK(cudaMalloc(&d_sr, sizeof(int) * n_sr));
     CUDA_OK(cudaMemcpy(d_sr, sr.data(), sizeof(int) * n_sr, cudaMemcpyHostToDevice));
   }
+  sr_cap = SrCaps{};
+  if (n_sr) {
+    // shared memory of the CG kernel grows with the band height: wide images need the
+    // larger cluster
+    auto caps_for = [&](int ncta) {
+      SrCaps m;
+      for (int p : sr) {
+        const ProbDev &d = pds[p];
+        SrCaps c;
+        sr_caps(d.H, d.W, d.scale, d.kh, d.kw, ncta, &c);
+        m.taps = std::max(m.taps, c.taps);
+        m.rows = std::max(m.rows, c.rows);
+        m.zrows = std::max(m.zrows, c.zrows);
+        m.cols = std::max(m.cols, c.cols);
+        m.zfloats = std::max(m.zfloats, c.zfloats);
+        m.band = std::max(m.band, c.band);
+        m.spec737 = m.spec737 && c.spec737;
+      }
+      return m;
+    };
+    const int sr_limit = 227 * 1024;
+    if (lc.sr_cluster < 1 || lc.sr_cluster > 16) lc.sr_cluster = 8;
+    sr_cap = caps_for(lc.sr_cluster);
+    if (sr_smem_bytes(sr_cap, 0) > sr_limit && lc.sr_cluster < 16) {
+      lc.sr_cluster = 16;
+      sr_cap = caps_for(16);
+    }
+    if (sr_smem_bytes(sr_cap, 0) > sr_limit)
+      throw Fail{RED_EUNSUPPORTED, "super-resolution image too large for the CG kernel's shared memory"};
+    const int act0 = sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, 0));
+    if (act0 < 1) throw Fail{RED_EUNSUPPORTED, "the CG kernel's cluster does not fit on this device"};
+    // the band's vectors in shared memory when they fit and as many clusters stay resident
+    // as the launch needs
+    const int smem1 = sr_smem_bytes(sr_cap, 1);
+    sr_cap.resident = (smem1 <= sr_limit &&
+                       sr_max_active_clusters(lc.sr_cluster, smem1) >= std::min(n_sr, act0)) ? 1 : 0;
+  }
   n_fused = (int)fused.size();
   if (n_fused) {
     CUDA_OK(cudaMalloc(&d_fused, sizeof(int) * n_fused));
@@ -246,7 +290,7 @@ void prepare_launch_attrs(const Plan &pl) {
     CUDA_OK(fft_cluster_prepare(fft_cluster_smem(pl.fused_tw_m, pl.fused_tw_h, pl.fused_a, pl.fused_buf),
                                 pl.fused_ncta));
   if (pl.n_rows) CUDA_OK(fft_prepare(pl.row_tw_cap, pl.row_buf_cap, pl.col_tw_cap, pl.col_buf_cap));
-  if (pl.n_sr) CUDA_OK(sr_prepare(pl.lc.sr_cluster));
+  if (pl.n_sr) CUDA_OK(sr_prepare(pl.lc.sr_cluster, sr_smem_bytes(pl.sr_cap, pl.sr_cap.resident)));
 }
 
 void Plan::release() {
@@ -279,7 +323,7 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
   CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s,
                      nullptr, pl.lc.nlm_occ));
   launch_fft_solve(d_probs, pl, sa, s);
-  if (pl.n_sr) CUDA_OK(launch_sr_step(d_probs, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, sa, s));
+  if (pl.n_sr) CUDA_OK(launch_sr_step(d_probs, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, pl.sr_cap, sa, s));
 }
 
 // One extrapolation (Algorithm 1 / RRE) over every problem of a plan.
@@ -477,6 +521,7 @@ red_status red_create_problem(const red_config *cfg, const void *y_dev, void *st
     CUDA_OK(cudaMallocHost(&P->h_pinned, 4096));
     fill_prob_dev(P.get());
     if (fft_cluster_override() >= 0) P->lc.fft_cluster = fft_cluster_override();
+    if (sr_cluster_override() > 0) P->lc.sr_cluster = sr_cluster_override();
     problem_upload_pd(P.get());
     char *b = static_cast<char *>(P->block);
     CUDA_OK(cudaMemcpyAsync(b + P->L.psf, P->psf.data(), sizeof(float) * P->psf.size(),

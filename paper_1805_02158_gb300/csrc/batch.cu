@@ -104,7 +104,7 @@ std::string tune_key(const red_batch_s *b) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  key << "v3|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  key << "v4|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
   for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
   std::string k = key.str();
   std::replace(k.begin(), k.end(), ' ', '_');
@@ -220,12 +220,14 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   if (has_sr) {
     float bt = 1e30f;
     LaunchCfg c = best;
-    for (int cl : {4, 8}) {
+    for (int cl : {8, 16}) {
       c.sr_cluster = cl;
       rebuild(c);
       const Plan &pl = b->plan;
+      if (pl.lc.sr_cluster != cl) continue;   // the plan had to change it
+      prepare_launch_attrs(pl);
       const float t = time_ms(s, 1, [&] {
-        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, cl, sa, s));
+        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, cl, pl.sr_cap, sa, s));
       });
       if (t < bt) { bt = t; best.sr_cluster = cl; }
     }
@@ -276,7 +278,7 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
       }
       if (pl.n_sr) {
         ps.begin(RED_PHASE_CG);
-        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, sa, s));
+        CUDA_OK(launch_sr_step(b->d_pds, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, pl.sr_cap, sa, s));
         ps.end();
       }
     } else {
@@ -306,6 +308,7 @@ void ensure_ready(red_batch_s *b, cudaStream_t s) {
       tune_store(b->tune_key, c);
     }
     if (fft_cluster_override() >= 0) c.fft_cluster = fft_cluster_override();
+    if (sr_cluster_override() > 0) c.sr_cluster = sr_cluster_override();
     b->lc = c;
     b->plan.build(b->pds, c);
     upload_pds(b);

@@ -138,8 +138,21 @@ cudaError_t launch_convert_to_slot(const ProbDev *d_prob, const float *src, int 
                                    cudaStream_t s);
 cudaError_t launch_fetch_slot(const ProbDev *d_prob, int slot, float *dst, cudaStream_t s);
 cudaError_t launch_sr_rhs(const ProbDev *d_prob, const float *y, cudaStream_t s);
+// Shared-memory extents (4-byte words) of the super-resolution CG kernel.
+struct SrCaps {
+  int taps = 0;      // kh * kw
+  int rows = 0;      // row-window entries of a band (band rows + kh - 1)
+  int zrows = 0;     // LR rows of z kept by a band
+  int cols = 0;      // W + kw - 1
+  int zfloats = 0;   // zrows * lw
+  int band = 0;      // pixels of the largest band
+  int spec737 = 1;   // every problem has a 7x7 PSF and scale 3 (specialised kernel)
+  int resident = 0;  // the band's CG vectors are kept in shared memory
+};
+void sr_caps(int H, int W, int scale, int kh, int kw, int ncta, SrCaps *c);
+int sr_smem_bytes(const SrCaps &c, int resident);
 cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_sr,
-                           int cluster, StepArgs sa, cudaStream_t s);
+                           int cluster, const SrCaps &caps, StepArgs sa, cudaStream_t s);
 cudaError_t launch_objective(const ProbDev *d_prob, const float *x, const float *hx,
                              const float *y, const float *f, double *out, cudaStream_t s);
 
@@ -156,7 +169,8 @@ int fft_smem_cols(int tw_cap, int buf_cap);
 
 void count_launches(uint64_t n);
 cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col_buf_cap);
-cudaError_t sr_prepare(int cluster);
+cudaError_t sr_prepare(int cluster, int smem);
+int sr_max_active_clusters(int cluster, int smem);
 cudaError_t nlm_prepare(int wy);
 
 // ---- small device helpers ---------------------------------------------------------------

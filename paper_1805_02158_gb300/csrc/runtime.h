@@ -66,6 +66,7 @@ struct Plan {
   int n_nlm = 0, n_rows = 0, n_cols = 0, n_chunks = 0, n_sr = 0;
   int off_nlm = 0, off_rows = 0, off_cols = 0, off_chunks = 0;
   int row_tw_cap = 0, row_buf_cap = 0, col_tw_cap = 0, col_buf_cap = 0;
+  SrCaps sr_cap;              // shared-memory extents of the super-resolution CG launch
   std::vector<int> n_row_items;
   void build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg);
   void release();
@@ -89,6 +90,7 @@ void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaS
 std::vector<CycleOp> cycle_ops(int ve, int k, int m);
 void prepare_launch_attrs(const Plan &pl);
 int fft_cluster_override();   // RED_FFT_CLUSTER, or -1 when unset
+int sr_cluster_override();    // RED_SR_CLUSTER (8 or 16), or -1 when unset
 
 }  // namespace red
 

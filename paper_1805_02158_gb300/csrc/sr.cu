@@ -5,17 +5,27 @@
 // is solved by textbook conjugate gradients, cg_iters iterations, warm-started at x_k,
 // residual formed afresh from b - A x_k (same sequence as the FP64 oracle).
 //
-// GB300 mapping: one thread-block cluster per problem (8 CTAs by default). Each CTA owns
-// a band of image rows (and the low-resolution rows whose samples fall in it). The
-// operator is applied as two fused passes per iteration,
-//     z = S B p             (LR samples of the band; kh*kw taps each)
-//     A p = B^T S^T z / sigma^2 + alpha p   (each HR pixel gathers the ~(kh/s)(kw/s)
-//                                            LR samples its adjoint blur touches)
-// with the vectors in global memory (L2 resident) and the dot products exchanged through
-// distributed shared memory: every CTA writes its partial, and after a cluster barrier
-// every CTA sums all partials in rank order, so all CTAs hold the same alpha/beta with no
-// atomics and a fixed reduction order. Cluster barriers are hardware barriers.
+// GB300 mapping: one thread-block cluster per problem (8 or 16 CTAs, autotuned). CTA q
+// owns a band of HR rows. A p = B^T S^T z / sigma^2 + alpha p with z = S B p needs, for
+// the band, the LR rows of z whose samples the adjoint blur of the band touches; each CTA
+// keeps exactly those rows of z (its own and a halo of at most ceil(kh/s) rows) in shared
+// memory. z is never formed from p: since p_{i+1} = r_{i+1} + beta p_i and S B is linear,
+//     z_{i+1} = S B r_{i+1} + beta z_i,
+// and r_{i+1} is final in every band once the r.r reduction's cluster barrier has passed.
+// So one CG iteration is
+//     A p (band, from shared z)  ->  p.Ap      [cluster barrier 1]
+//     x += a p, r -= a Ap (band)  ->  r.r      [cluster barrier 2]
+//     p = r + beta p (band);  z = S B r + beta z (band + halo rows, r read from the L2)
+// with two barriers. The adjoint pass loops, per HR row, only over the kernel taps that
+// hit LR samples: lanes of a warp take columns of one residue mod s, so every lane has the
+// same taps and consecutive LR columns. Dot products: each warp's partial goes to shared
+// memory; after the barrier every warp reads all partials of the cluster through
+// distributed shared memory and sums them in one fixed order, so all CTAs hold identical
+// alpha and beta (no atomics). x, r, p, Ap stay in global memory (L2 resident), each CTA
+// touching only its band except for the halo rows of r.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -26,52 +36,14 @@ namespace red {
 namespace {
 
 constexpr int kSrThreads = 256;
+constexpr int kSrWarps = kSrThreads / 32;
+constexpr int kSrMaxCluster = 16;
+constexpr unsigned kFullMask = 0xffffffffu;
 
-// Block-wide sum of a float (fixed order); all threads get the result.
-__device__ float block_sum(float v, float *scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();
-  if (lane == 0) scratch[warp] = v;
-  __syncthreads();
-  float t = 0.f;
-  const int nw = blockDim.x >> 5;
-  for (int w = 0; w < nw; ++w) t += scratch[w];
-  return t;
-}
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Sum over the cluster's CTAs of each CTA's `part` (shared variable), rank order.
-__device__ double cluster_sum(cg::cluster_group &cl, float *part) {
-  double s = 0.0;
-  const int n = cl.num_blocks();
-  for (int r = 0; r < n; ++r) s += (double)*cl.map_shared_rank(part, r);
-  return s;
-}
-
-// z = S B v on LR rows [i0, i1)
-__device__ void apply_sb(const ProbDev *P, const float *v, float *z, int i0, int i1) {
-  const int H = P->H, W = P->W, s = P->scale, lw = P->lw, kh = P->kh, kw = P->kw;
-  const int c1 = (kh - 1) / 2, c2 = (kw - 1) / 2;
-  const int n = (i1 - i0) * lw;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const int i = i0 + t / lw, j = t % lw;
-    const int u = s * i, w = s * j;
-    float acc = 0.f;
-    for (int a = 0; a < kh; ++a) {
-      const int rr = ((u - (a - c1)) % H + H) % H;
-      const float *row = v + (long)rr * W;
-      const float *taps = P->psf + a * kw;
-      for (int b = 0; b < kw; ++b) {
-        const int cc = ((w - (b - c2)) % W + W) % W;
-        acc = fmaf(taps[b], row[cc], acc);
-      }
-    }
-    z[(long)i * lw + j] = acc;
-  }
-}
-
-// out(u,v) = (B^T S^T z)(u,v) for HR pixel (u,v)
+// out(u,v) = (B^T S^T z)(u,v) for HR pixel (u,v), z an LR image in global memory
+// (the right-hand side B^T S^T y; once per observation).
 __device__ __forceinline__ float apply_btst(const ProbDev *P, const float *z, int u, int v) {
   const int H = P->H, W = P->W, s = P->scale, lh = P->lh, lw = P->lw, kh = P->kh, kw = P->kw;
   const int c1 = (kh - 1) / 2, c2 = (kw - 1) / 2;
@@ -90,104 +62,505 @@ __device__ __forceinline__ float apply_btst(const ProbDev *P, const float *z, in
   return acc;
 }
 
-__global__ void __launch_bounds__(kSrThreads)
-k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, StepArgs sa) {
-  __shared__ float scratch[32];
-  __shared__ float part_a, part_b, part_c, part_d, part_e;
+// Shared-memory tables of one CTA.
+struct SrBand {
+  int H, W, s, lh, lw, kh, kw, c1, c2;
+  int r0, nb;            // HR rows [r0, r0 + nb)
+  int T;                 // rowmap entries: unwrapped rows r0 - c1 + t, t < T = nb + kh - 1
+  int nz;                // z rows kept
+  int vlo, vhi;          // interior columns of the adjoint pass (no wrap, all samples valid)
+  const float *taps;     // kh * kw
+  const int *rowmap;     // t -> z row index, or -1
+  const int *lrow;       // z row index -> LR row
+  const int *colmap;     // c < W + kw - 1: LR column of wrapped HR column c - c2, or -1
+  float *z;              // nz x lw
+};
+
+// Deterministic sum over the cluster of one float per warp (all warps get the result):
+// each lane adds a fixed subset in a fixed order, then a fixed xor tree. FP32 only (the
+// FP64 units of this part are a small fraction of the FP32 ones, and the CG scalars are
+// FP32 quantities).
+__device__ __forceinline__ float cluster_total(cg::cluster_group &cl, float *slot, float v, int ncta) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFullMask, v, off);
+  if (lane == 0) slot[warp] = v;
+  cl.sync();
+  constexpr int kPer = kSrMaxCluster * kSrWarps / 32;
+  float got[kPer];
+  const int n = ncta * kSrWarps;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int i = lane + 32 * t;
+    got[t] = i < n ? *cl.map_shared_rank(slot + (i % kSrWarps), i / kSrWarps) : 0.f;
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) acc += got[t];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFullMask, acc, off);
+  return acc;
+}
+
+// Compile-time kernel extents where known (the x3 / 7x7 workload), else the runtime ones.
+template <int KH, int KW, int S>
+struct SrDims {
+  int kh, kw, s;
+  __device__ __forceinline__ explicit SrDims(const SrBand &g)
+      : kh(KH ? KH : g.kh), kw(KW ? KW : g.kw), s(S ? S : g.s) {}
+};
+
+// acc += sum_b taps[b] row[w0 - b] (no wrap), kw taps.
+template <int KW>
+__device__ __forceinline__ float row_taps(const float *ta, const float *row, int w0, int kw, float acc) {
+  if constexpr (KW > 0) {
+#pragma unroll
+    for (int b = 0; b < KW; ++b) acc = fmaf(ta[b], row[w0 - b], acc);
+  } else {
+    for (int b = 0; b < kw; ++b) acc = fmaf(ta[b], row[w0 - b], acc);
+  }
+  return acc;
+}
+
+// z (rows kept by the band) = S B v, or S B v + beta z when accumulate; v in global memory.
+template <int KH, int KW, int S>
+__device__ void band_sb(const SrBand &g, const float *__restrict__ v, float beta, bool accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const SrDims<KH, KW, S> d(g);
+  const int W = g.W, c1 = g.c1, c2 = g.c2;
+  for (int k = warp; k < g.nz; k += kSrWarps) {
+    const int li = g.lrow[k];
+    float *zr = g.z + (long)k * g.lw;
+    for (int j = lane; j < g.lw; j += 32) {
+      const int w0 = d.s * j + c2;                 // HR column of tap b = 0
+      const bool inner = (w0 - (d.kw - 1) >= 0) && (w0 <= W - 1);
+      float acc = 0.f;
+      if (inner) {
+        if constexpr (KH > 0) {
+#pragma unroll
+          for (int a = 0; a < KH; ++a)
+            acc = row_taps<KW>(g.taps + a * d.kw, v + (long)wrap1(d.s * li - a + c1, g.H) * W, w0,
+                               d.kw, acc);
+        } else {
+          for (int a = 0; a < d.kh; ++a)
+            acc = row_taps<KW>(g.taps + a * d.kw, v + (long)wrap1(d.s * li - a + c1, g.H) * W, w0,
+                               d.kw, acc);
+        }
+      } else {
+        for (int a = 0; a < d.kh; ++a) {
+          const float *row = v + (long)wrap1(d.s * li - a + c1, g.H) * W;
+          const float *ta = g.taps + a * d.kw;
+          for (int b = 0; b < d.kw; ++b) acc = fmaf(ta[b], row[wrap1(w0 - b, W)], acc);
+        }
+      }
+      zr[j] = accumulate ? fmaf(beta, zr[j], acc) : acc;
+    }
+  }
+}
+
+// acc += sum_t ta[t s] zr[t] over the column taps b = b0 + t s < kw of one residue.
+template <int KW, int S>
+__device__ __forceinline__ float col_taps(const float *ta, const float *zr, int b0, int kw, int s,
+                                          float acc) {
+  if constexpr (KW > 0 && S > 0) {
+#pragma unroll
+    for (int t = 0; t < (KW + S - 1) / S; ++t)
+      if (b0 + t * S < KW) acc = fmaf(ta[t * S], zr[t], acc);
+  } else {
+    for (int t = 0; b0 + t * s < kw; ++t) acc = fmaf(ta[t * s], zr[t], acc);
+  }
+  return acc;
+}
+
+// For every pixel of the band: epi(e, l, (B^T S^T z)(e)), e the image index, l = e - r0 W.
+// Lanes take columns of one residue mod s (any extents).
+template <int KH, int KW, int S, class Epi>
+__device__ __forceinline__ void band_adjoint_residue(const SrBand &g, Epi &&epi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const SrDims<KH, KW, S> d(g);
+  const int W = g.W, c2 = g.c2, lw = g.lw;
+  // interior: warp item = (row, residue ph of the column mod s); the row's sampled taps
+  // and the residue's column taps are the same for every lane
+  if (g.vhi >= g.vlo) {
+    for (int it = warp; it < g.nb * d.s; it += kSrWarps) {
+      const int ul = it / d.s, ph = it - ul * d.s;
+      const int qlo = (g.vlo - ph + d.s - 1) / d.s;                 // vlo >= c2 >= 0
+      const int qhi = g.vhi >= ph ? (g.vhi - ph) / d.s : -1;
+      if (qlo > qhi) continue;
+      const int b0 = (c2 - ph + d.s) % d.s;                         // c2 - ph > -s
+      const int d0 = (ph + b0 - c2) / d.s;                          // exact
+      const long rowbase = (long)(g.r0 + ul) * W;
+      const int lbase = ul * W;
+      if constexpr (KH > 0) {
+        int zoff[KH];   // offset in z of tap row a's sampled LR row, or -1
+#pragma unroll
+        for (int a = 0; a < KH; ++a) {
+          const int zk = g.rowmap[ul + a];
+          zoff[a] = zk >= 0 ? zk * lw : -1;
+        }
+        for (int q = qlo + lane; q <= qhi; q += 32) {
+          float acc = 0.f;
+#pragma unroll
+          for (int a = 0; a < KH; ++a)
+            if (zoff[a] >= 0)
+              acc = col_taps<KW, S>(g.taps + a * d.kw + b0, g.z + zoff[a] + d0 + q, b0, d.kw, d.s, acc);
+          epi(rowbase + d.s * q + ph, lbase + d.s * q + ph, acc);
+        }
+      } else {
+        for (int q = qlo + lane; q <= qhi; q += 32) {
+          float acc = 0.f;
+          for (int a = 0; a < d.kh; ++a) {
+            const int zk = g.rowmap[ul + a];
+            if (zk >= 0)
+              acc = col_taps<KW, S>(g.taps + a * d.kw + b0, g.z + zk * lw + d0 + q, b0, d.kw, d.s, acc);
+          }
+          epi(rowbase + d.s * q + ph, lbase + d.s * q + ph, acc);
+        }
+      }
+    }
+  }
+  // edge columns (wrap-around or past the last LR sample): every tap checked
+  const int nle = g.vhi >= g.vlo ? g.vlo : W;
+  const int ne = g.vhi >= g.vlo ? g.vlo + (W - 1 - g.vhi) : W;
+  for (int idx = threadIdx.x; idx < g.nb * ne; idx += kSrThreads) {
+    const int ul = idx / ne, ei = idx - ul * ne;
+    const int v = ei < nle ? ei : g.vhi + 1 + (ei - nle);
+    float acc = 0.f;
+    for (int a = 0; a < d.kh; ++a) {
+      const int zk = g.rowmap[ul + a];
+      if (zk < 0) continue;
+      const float *zr = g.z + (long)zk * lw;
+      const float *ta = g.taps + a * d.kw;
+      for (int b = 0; b < d.kw; ++b) {
+        const int cj = g.colmap[v + b];
+        if (cj >= 0) acc = fmaf(ta[b], zr[cj], acc);
+      }
+    }
+    epi((long)(g.r0 + ul) * W + v, ul * W + v, acc);
+  }
+}
+
+
+__host__ __device__ constexpr int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// The same for compile-time extents: a lane takes S consecutive columns S q .. S q + S - 1,
+// which together use every tap of a sampled row once and LR columns q + DMIN .. q + DMAX.
+template <int KH, int KW, int S, class Epi>
+__device__ __forceinline__ void band_adjoint_blocked(const SrBand &g, Epi &&epi) {
+  constexpr int C2 = (KW - 1) / 2;
+  constexpr int DMIN = floor_div(-C2, S), DMAX = floor_div(S - 1 + KW - 1 - C2, S);
+  constexpr int ND = DMAX - DMIN + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int W = g.W, lw = g.lw;
+  // groups whose S columns are all interior
+  const int glo = (g.vlo + S - 1) / S;
+  const int ghi = g.vhi >= S - 1 ? (g.vhi - (S - 1)) / S : -1;
+  for (int ul = warp; ul < g.nb; ul += kSrWarps) {
+    int zoff[KH];
+#pragma unroll
+    for (int a = 0; a < KH; ++a) {
+      const int zk = g.rowmap[ul + a];
+      zoff[a] = zk >= 0 ? zk * lw : -1;
+    }
+    const long rowbase = (long)(g.r0 + ul) * W;
+    const int lbase = ul * W;
+    for (int q = glo + lane; q <= ghi; q += 32) {
+      float acc[S];
+#pragma unroll
+      for (int ph = 0; ph < S; ++ph) acc[ph] = 0.f;
+#pragma unroll
+      for (int a = 0; a < KH; ++a) {
+        if (zoff[a] < 0) continue;
+        const float *zr = g.z + zoff[a] + q;
+        float zv[ND];
+#pragma unroll
+        for (int i = 0; i < ND; ++i) zv[i] = zr[DMIN + i];
+        const float *ta = g.taps + a * KW;
+#pragma unroll
+        for (int b = 0; b < KW; ++b) {
+          const float t = ta[b];
+#pragma unroll
+          for (int ph = 0; ph < S; ++ph)
+            if ((ph + b - C2 - DMIN * S) % S == 0)
+              acc[ph] = fmaf(t, zv[floor_div(ph + b - C2, S) - DMIN], acc[ph]);
+        }
+      }
+#pragma unroll
+      for (int ph = 0; ph < S; ++ph) epi(rowbase + S * q + ph, lbase + S * q + ph, acc[ph]);
+    }
+  }
+  // the remaining columns, every tap checked
+  const int nle = ghi >= glo ? S * glo : W;
+  const int ne = ghi >= glo ? nle + (W - S * (ghi + 1)) : W;
+  for (int idx = threadIdx.x; idx < g.nb * ne; idx += kSrThreads) {
+    const int ul = idx / ne, ei = idx - ul * ne;
+    const int v = ei < nle ? ei : S * (ghi + 1) + (ei - nle);
+    float acc = 0.f;
+    for (int a = 0; a < KH; ++a) {
+      const int zk = g.rowmap[ul + a];
+      if (zk < 0) continue;
+      const float *zr = g.z + (long)zk * lw;
+      const float *ta = g.taps + a * KW;
+#pragma unroll
+      for (int b = 0; b < KW; ++b) {
+        const int cj = g.colmap[v + b];
+        if (cj >= 0) acc = fmaf(ta[b], zr[cj], acc);
+      }
+    }
+    epi((long)(g.r0 + ul) * W + v, ul * W + v, acc);
+  }
+}
+
+template <int KH, int KW, int S, class Epi>
+__device__ __forceinline__ void band_adjoint(const SrBand &g, Epi &&epi) {
+  if constexpr (KH > 0 && KW > 0 && S > 0)
+    band_adjoint_blocked<KH, KW, S>(g, epi);
+  else
+    band_adjoint_residue<KH, KW, S>(g, epi);
+}
+
+// Shared memory (4-byte words): taps | rowmap | lrow | colmap | z | 2 x per-warp partials
+// | (resident bands only) x, r, p, Ap of the band. The caps are maxima over the launch's
+// problems (sr_caps on the host). When the band's vectors do not fit (large images) they
+// stay in global memory and every loop batches its loads.
+template <int KH, int KW, int S>
+__global__ void __launch_bounds__(kSrThreads, 2)
+k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, StepArgs sa,
+          SrCaps caps, int resident) {
+  extern __shared__ float sm_sr[];
+  __shared__ int nz_sh, is_last;
+  __shared__ float part_d[kSrWarps], part_x[kSrWarps];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
   const ProbDev *P = probs + sr_list[blockIdx.x / ncta];
   if (sa.update_state && P->st->done) return;   // uniform over the cluster
+  const int tid = threadIdx.x;
 
-  const int H = P->H, W = P->W, s = P->scale, lh = P->lh;
-  const int rb0 = (int)((long)rank * H / ncta), rb1 = (int)((long)(rank + 1) * H / ncta);
-  const int i0 = min(lh, (rb0 + s - 1) / s), i1 = min(lh, (rb1 + s - 1) / s);
-  const long e0 = (long)rb0 * W, e1 = (long)rb1 * W;
+  SrBand g;
+  g.H = P->H; g.W = P->W; g.s = P->scale; g.lh = P->lh; g.lw = P->lw; g.kh = P->kh; g.kw = P->kw;
+  g.c1 = (g.kh - 1) / 2;
+  g.c2 = (g.kw - 1) / 2;
+  g.r0 = (int)((long)rank * g.H / ncta);
+  g.nb = (int)((long)(rank + 1) * g.H / ncta) - g.r0;
+  g.T = g.nb + g.kh - 1;
+  g.vlo = g.c2;
+  g.vhi = min(g.W - 1, g.s * (g.lw - 1)) - (g.kw - 1 - g.c2);
+  float *taps = sm_sr;
+  int *rowmap = reinterpret_cast<int *>(taps + caps.taps);
+  int *lrow = rowmap + caps.rows;
+  int *colmap = lrow + caps.zrows;
+  g.z = reinterpret_cast<float *>(colmap + caps.cols);
+  float *slot_a = g.z + caps.zfloats;
+  float *slot_b = slot_a + kSrWarps;
+  g.taps = taps;
+  g.rowmap = rowmap;
+  g.lrow = lrow;
+  g.colmap = colmap;
+
+  for (int i = tid; i < g.kh * g.kw; i += kSrThreads) taps[i] = P->psf[i];
+  for (int t = tid; t < g.T; t += kSrThreads) {
+    const int R = wrap1(g.r0 - g.c1 + t, g.H);
+    rowmap[t] = (R % g.s == 0 && R / g.s < g.lh) ? R / g.s : -1;
+  }
+  for (int c = tid; c < g.W + g.kw - 1; c += kSrThreads) {
+    const int C = wrap1(c - g.c2, g.W);
+    colmap[c] = (C % g.s == 0 && C / g.s < g.lw) ? C / g.s : -1;
+  }
+  __syncthreads();
+  if (tid == 0) {   // compact the sampled rows (T is at most a few hundred)
+    int nz = 0;
+    for (int t = 0; t < g.T; ++t)
+      if (rowmap[t] >= 0) {
+        lrow[nz] = rowmap[t];
+        rowmap[t] = nz++;
+      }
+    nz_sh = nz;
+  }
+  __syncthreads();
+  g.nz = nz_sh;
+
   const float alpha = P->alpha, is2 = P->inv_sigma2;
-  float *x = P->cg_x, *r = P->cg_r, *p = P->cg_p, *ap = P->cg_ap, *z = P->cg_z;
+  const long e0 = (long)g.r0 * g.W;
+  const int nl = g.nb * g.W;                    // pixels of the band
+  float *r_g = P->cg_r;                         // r in global memory (halo rows for S B r)
+  // band vectors, indexed by the band-local pixel index
+  float *xs, *rs, *ps, *aps;
+  if (resident) {
+    xs = slot_b + kSrWarps;
+    rs = xs + caps.band;
+    ps = rs + caps.band;
+    aps = ps + caps.band;
+  } else {
+    xs = P->cg_x + e0;
+    rs = r_g + e0;
+    ps = P->cg_p + e0;
+    aps = P->cg_ap + e0;
+  }
   const float *f = P->f, *b0 = P->b0;
-
   const int esz = P->storage ? 2 : 4;
   const void *xin = sa.src_ptr ? sa.src_ptr
                                : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
   const int in_bf16 = sa.src_ptr ? 0 : P->storage;
+  constexpr int kU = 4;   // elements per thread per batch of independent loads
 
-  // x = x_k (warm start)
-  for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) x[e] = load_img(xin, e, in_bf16);
-  cl.sync();
-  // r = b - A x, p = r
-  apply_sb(P, x, z, i0, i1);
-  cl.sync();
-  float acc = 0.f;
-  for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int u = (int)(e / W), v = (int)(e % W);
-    const float ax = fmaf(apply_btst(P, z, u, v), is2, alpha * x[e]);
-    const float rv = fmaf(alpha, f[e], b0[e]) - ax;
-    r[e] = rv;
-    p[e] = rv;
-    acc = fmaf(rv, rv, acc);
+  // x = x_k (warm start) into the band and global memory (S B x reads the halo rows)
+  for (int l0 = tid; l0 < nl; l0 += kU * kSrThreads) {
+    float v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int l = l0 + u * kSrThreads;
+      if (l < nl) v[u] = load_img(xin, e0 + l, in_bf16);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int l = l0 + u * kSrThreads;
+      if (l < nl) {
+        xs[l] = v[u];
+        P->cg_x[e0 + l] = v[u];
+      }
+    }
   }
-  acc = block_sum(acc, scratch);
-  if (threadIdx.x == 0) part_a = acc;
   cl.sync();
-  double rr = cluster_sum(cl, &part_a);
+  band_sb<KH, KW, S>(g, P->cg_x, 0.f, false);
+  __syncthreads();
+  float dot = 0.f;
+  // r = b - A x, p = r
+  band_adjoint<KH, KW, S>(g, [&](long e, int l, float acc) {
+    const float ax = fmaf(acc, is2, alpha * xs[l]);
+    const float rv = fmaf(alpha, f[e], b0[e]) - ax;
+    rs[l] = rv;
+    if (resident) r_g[e] = rv;
+    ps[l] = rv;
+    dot = fmaf(rv, rv, dot);
+  });
+  float rr = cluster_total(cl, slot_b, dot, ncta);
+  band_sb<KH, KW, S>(g, r_g, 0.f, false);   // z = S B p, p = r
+  __syncthreads();
 
   for (int it = 0; it < P->cg_iters; ++it) {
-    if (rr == 0.0) break;
-    apply_sb(P, p, z, i0, i1);
-    cl.sync();
-    acc = 0.f;
-    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int u = (int)(e / W), v = (int)(e % W);
-      const float apv = fmaf(apply_btst(P, z, u, v), is2, alpha * p[e]);
-      ap[e] = apv;
-      acc = fmaf(p[e], apv, acc);
+    if (rr == 0.f) break;
+    dot = 0.f;
+    band_adjoint<KH, KW, S>(g, [&](long e, int l, float acc) {
+      const float pv = ps[l];
+      const float apv = fmaf(acc, is2, alpha * pv);
+      aps[l] = apv;
+      dot = fmaf(pv, apv, dot);
+    });
+    const float pap = cluster_total(cl, slot_a, dot, ncta);
+    if (pap <= 0.f) break;
+    const float a = rr / pap;
+    dot = 0.f;
+    for (int l0 = tid; l0 < nl; l0 += kU * kSrThreads) {
+      float pv[kU], av[kU], rv[kU], xv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int l = l0 + u * kSrThreads;
+        if (l < nl) {
+          pv[u] = ps[l];
+          av[u] = aps[l];
+          rv[u] = rs[l];
+          xv[u] = xs[l];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int l = l0 + u * kSrThreads;
+        if (l < nl) {
+          xs[l] = fmaf(a, pv[u], xv[u]);
+          const float rn = fmaf(-a, av[u], rv[u]);
+          rs[l] = rn;
+          if (resident) r_g[e0 + l] = rn;
+          dot = fmaf(rn, rn, dot);
+        }
+      }
     }
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) part_b = acc;
-    cl.sync();
-    const double pap = cluster_sum(cl, &part_b);
-    if (pap <= 0.0) break;
-    const float a = (float)(rr / pap);
-    acc = 0.f;
-    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      x[e] = fmaf(a, p[e], x[e]);
-      const float rv = fmaf(-a, ap[e], r[e]);
-      r[e] = rv;
-      acc = fmaf(rv, rv, acc);
-    }
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) part_c = acc;
-    cl.sync();
-    const double rr_new = cluster_sum(cl, &part_c);
-    const float beta = (float)(rr_new / rr);
+    const float rr_new = cluster_total(cl, slot_b, dot, ncta);
+    const float beta = rr_new / rr;
     rr = rr_new;
-    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) p[e] = fmaf(beta, p[e], r[e]);
-    cl.sync();
+    for (int l0 = tid; l0 < nl; l0 += kU * kSrThreads) {
+      float pv[kU], rv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int l = l0 + u * kSrThreads;
+        if (l < nl) {
+          pv[u] = ps[l];
+          rv[u] = rs[l];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int l = l0 + u * kSrThreads;
+        if (l < nl) ps[l] = fmaf(beta, pv[u], rv[u]);
+      }
+    }
+    band_sb<KH, KW, S>(g, r_g, beta, true);   // z = S B r + beta z = S B p
+    __syncthreads();
   }
+  cl.sync();   // every CTA has finished its remote reads of the last reduction's partials
 
-  // write x_{k+1}, statistics against x_k
+  // x_{k+1} -> destination, statistics against x_k
   void *dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
   float sd = 0.f, sx = 0.f;
-  for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    float xv = x[e];
-    if (sa.dst_ptr) {
-      sa.dst_ptr[e] = xv;
-    } else {
-      store_img(dst_ring, e, xv, P->storage);
-      if (P->storage) xv = __bfloat162float(__float2bfloat16_rn(xv));
+  for (int l0 = tid; l0 < nl; l0 += kU * kSrThreads) {
+    float xv[kU], xo[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int l = l0 + u * kSrThreads;
+      if (l < nl) {
+        xv[u] = xs[l];
+        xo[u] = load_img(xin, e0 + l, in_bf16);
+      }
     }
-    const float xo = load_img(xin, e, in_bf16);
-    sd = fmaf(xv - xo, xv - xo, sd);
-    sx = fmaf(xo, xo, sx);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int l = l0 + u * kSrThreads;
+      if (l < nl) {
+        float v = xv[u];
+        if (sa.dst_ptr) {
+          sa.dst_ptr[e0 + l] = v;
+        } else {
+          store_img(dst_ring, e0 + l, v, P->storage);
+          if (P->storage) v = __bfloat162float(__float2bfloat16_rn(v));
+        }
+        sd = fmaf(v - xo[u], v - xo[u], sd);
+        sx = fmaf(xo[u], xo[u], sx);
+      }
+    }
   }
-  sd = block_sum(sd, scratch);
-  sx = block_sum(sx, scratch);
-  if (threadIdx.x == 0) { part_e = sd; part_d = sx; }
-  cl.sync();
-  if (sa.update_state && rank == 0 && threadIdx.x == 0) {
-    const double tsd = cluster_sum(cl, &part_e), tsx = cluster_sum(cl, &part_d);
+  if (!sa.update_state) return;
+  // CTA sums (fixed order), then the last CTA of the cluster to arrive sums them in rank
+  // order and runs the termination test
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sd += __shfl_xor_sync(kFullMask, sd, off);
+    sx += __shfl_xor_sync(kFullMask, sx, off);
+  }
+  if (lane == 0) {
+    part_d[warp] = sd;
+    part_x[warp] = sx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float td = 0.f, tx = 0.f;
+    for (int w = 0; w < kSrWarps; ++w) {
+      td += part_d[w];
+      tx += part_x[w];
+    }
+    P->row_stats[rank] = make_float2(td, tx);
+    __threadfence();
+    is_last = atomicAdd(&P->st->counter, 1u) == (unsigned)(ncta - 1);
+  }
+  __syncthreads();
+  if (tid == 0 && is_last) {
+    __threadfence();
+    double tsd = 0.0, tsx = 0.0;
+    for (int q = 0; q < ncta; ++q) {
+      const float2 v = __ldcg(&P->row_stats[q]);
+      tsd += (double)v.x;
+      tsx += (double)v.y;
+    }
     ProbState *st = P->st;
     const double rel = tsx > 0.0 ? sqrt(tsd / tsx) : (tsd > 0.0 ? INFINITY : 0.0);
     st->rel_change = rel;
@@ -197,10 +570,10 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       st->converged = rel < st->tol ? 1 : 0;
       st->final_slot = sa.dst;
     }
+    st->counter = 0;
+    __threadfence();
   }
-  cl.sync();   // keep every CTA's shared memory alive until rank 0 has read it
 }
-
 // b0 = B^T S^T y / sigma^2
 __global__ void k_sr_rhs(const ProbDev *__restrict__ P, const float *__restrict__ y) {
   const long n = (long)P->H * P->W;
@@ -263,20 +636,80 @@ cudaError_t launch_sr_rhs(const ProbDev *d_prob, const float *y, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t sr_prepare(int cluster) {
-  if (cluster > 8)
-    return cudaFuncSetAttribute((const void *)k_sr_step,
-                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+// Shared-memory caps of one problem for a cluster of ncta CTAs (exact: the row windows
+// of every band are scanned as the kernel does).
+void sr_caps(int H, int W, int scale, int kh, int kw, int ncta, SrCaps *c) {
+  const int lh = H / scale, lw = W / scale, c1 = (kh - 1) / 2, c2 = (kw - 1) / 2;
+  (void)c2;
+  SrCaps o{};
+  o.spec737 = (kh == 7 && kw == 7 && scale == 3) ? 1 : 0;
+  o.taps = kh * kw;
+  o.cols = W + kw - 1;
+  for (int q = 0; q < ncta; ++q) {
+    const int r0 = (int)((long)q * H / ncta), nb = (int)((long)(q + 1) * H / ncta) - r0;
+    const int T = nb + kh - 1;
+    int nz = 0;
+    for (int t = 0; t < T; ++t) {
+      int R = r0 - c1 + t;
+      R = R < 0 ? R + H : (R >= H ? R - H : R);
+      if (R % scale == 0 && R / scale < lh) ++nz;
+    }
+    o.rows = std::max(o.rows, T);
+    o.band = std::max(o.band, nb * W);
+    o.zrows = std::max(o.zrows, nz);
+    o.zfloats = std::max(o.zfloats, nz * lw);
+  }
+  *c = o;
+}
+
+int sr_smem_bytes(const SrCaps &c, int resident) {
+  return 4 * (c.taps + c.rows + c.zrows + c.cols + c.zfloats + 2 * kSrWarps +
+              (resident ? 4 * c.band : 0));
+}
+
+cudaError_t sr_prepare(int cluster, int smem) {
+  for (const void *fn : {(const void *)k_sr_step<7, 7, 3>, (const void *)k_sr_step<0, 0, 0>}) {
+    cudaError_t e = cudaSuccess;
+    if (cluster > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(smem, 1));
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
+int sr_max_active_clusters(int cluster, int smem) {
+  if (sr_prepare(cluster, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(kSrThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_sr_step<0, 0, 0>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_sr, int cluster,
-                           StepArgs sa, cudaStream_t s) {
+                           const SrCaps &caps, StepArgs sa, cudaStream_t s) {
   if (n_sr <= 0) return cudaSuccess;
+  if (cluster < 1 || cluster > kSrMaxCluster) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_sr * cluster);
   cfg.blockDim = dim3(kSrThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = sr_smem_bytes(caps, caps.resident);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -285,7 +718,11 @@ cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_sr_step, d_probs, d_sr_probs, sa);
+  cudaError_t e = caps.spec737
+                      ? cudaLaunchKernelEx(&cfg, k_sr_step<7, 7, 3>, d_probs, d_sr_probs, sa, caps,
+                                           caps.resident)
+                      : cudaLaunchKernelEx(&cfg, k_sr_step<0, 0, 0>, d_probs, d_sr_probs, sa, caps,
+                                           caps.resident);
   count_launches(1);
   return e;
 }

@@ -149,15 +149,38 @@ def test_deblur_linear_solve_alone_matches_closed_form():
     assert rel_l2(to_host(out), ref) <= 1e-5
 
 
-@pytest.mark.parametrize("side", [48, 96])
-def test_sr_fp_step_matches_oracle(side):
+@pytest.mark.parametrize("cluster", ["8", "16"])
+@pytest.mark.parametrize("shape", [(48, 48), (96, 96), (54, 72)])
+def test_sr_fp_step_matches_oracle(shape, cluster, monkeypatch):
+    """One x3 SR FP step (NLM + 20 CG iterations), bands of 8 or 16 CTAs."""
     torch = torch_cuda()
-    p = synth.sr_x3(4, side)
+    monkeypatch.setenv("RED_SR_CLUSTER", cluster)
+    h, w = shape
+    p = synth.make_sr(4, h, w, synth.gaussian_psf(7, 1.6), 3, 5.0)
     P = red.Problem(red.config_for(p, cg_iters=20), to_dev(p.y))
     x = f32(p.x0)
-    out = torch.empty((side, side), device="cuda")
+    out = torch.empty((h, w), device="cuda")
     P.fp_step(to_dev(x), out)
-    ref = ofp.sr_fp_step(x, f32(p.y), oops.psf_otf(p.psf, (side, side)), 3, p.sigma, p.alpha, 20)
+    ref = ofp.sr_fp_step(x, f32(p.y), oops.psf_otf(p.psf, (h, w)), 3, p.sigma, p.alpha, 20)
+    assert rel_l2(to_host(out), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("side,cluster", [(256, "8"), (256, "16"), (1024, "16"), (384, "8")])
+def test_sr_linear_solve_alone_at_full_size(side, cluster, monkeypatch):
+    """The CG solve alone at the workload sizes: a constant image is a fixed point of the
+    denoiser (f(x) = x), so one FP step from x = c is 20 CG iterations on
+    (B^T S^T S B / s^2 + a I) x = B^T S^T y / s^2 + a c, warm-started at c."""
+    torch = torch_cuda()
+    monkeypatch.setenv("RED_SR_CLUSTER", cluster)
+    p = synth.make_sr(6, side, side, synth.gaussian_psf(7, 1.6), 3, 5.0,
+                      blur=lambda x: synth.circular_blur_separable(
+                          x, synth.gaussian_taps(7, 1.6), synth.gaussian_taps(7, 1.6)))
+    P = red.Problem(red.config_for(p, cg_iters=20), to_dev(p.y))
+    c = np.full((side, side), 80.0)
+    out = torch.empty((side, side), device="cuda")
+    P.fp_step(to_dev(c), out)
+    ref = ofp.sr_fp_step(c, f32(p.y), oops.psf_otf(p.psf, (side, side)), 3, p.sigma, p.alpha, 20,
+                         denoise=lambda v: v)
     assert rel_l2(to_host(out), ref) <= 1e-4
 
 
