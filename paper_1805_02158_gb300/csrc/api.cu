@@ -256,6 +256,7 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
         m.cols = std::max(m.cols, c.cols);
         m.zfloats = std::max(m.zfloats, c.zfloats);
         m.band = std::max(m.band, c.band);
+        m.band_ext = std::max(m.band_ext, c.band_ext);
         m.spec737 = m.spec737 && c.spec737;
       }
       return m;
@@ -269,13 +270,18 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
     }
     if (sr_smem_bytes(sr_cap, 0) > sr_limit)
       throw Fail{RED_EUNSUPPORTED, "super-resolution image too large for the CG kernel's shared memory"};
-    const int act0 = sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, 0));
+    const int sp = sr_cap.spec737;
+    const int act0 = sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, 0), sp, 2);
     if (act0 < 1) throw Fail{RED_EUNSUPPORTED, "the CG kernel's cluster does not fit on this device"};
     // the band's vectors in shared memory when they fit and as many clusters stay resident
     // as the launch needs
     const int smem1 = sr_smem_bytes(sr_cap, 1);
     sr_cap.resident = (smem1 <= sr_limit &&
-                       sr_max_active_clusters(lc.sr_cluster, smem1) >= std::min(n_sr, act0)) ? 1 : 0;
+                       sr_max_active_clusters(lc.sr_cluster, smem1, sp, 2) >= std::min(n_sr, act0)) ? 1 : 0;
+    // the larger register budget (one CTA per SM) when every cluster still fits at once
+    sr_cap.minb = 2;
+    if (sp && sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, sr_cap.resident), sp, 1) >= n_sr)
+      sr_cap.minb = 1;
   }
   n_fused = (int)fused.size();
   if (n_fused) {

@@ -15,14 +15,16 @@
 // So one CG iteration is
 //     A p (band, from shared z)  ->  p.Ap      [cluster barrier 1]
 //     x += a p, r -= a Ap (band)  ->  r.r      [cluster barrier 2]
-//     p = r + beta p (band);  z = S B r + beta z (band + halo rows, r read from the L2)
-// with two barriers. The adjoint pass loops, per HR row, only over the kernel taps that
-// hit LR samples: lanes of a warp take columns of one residue mod s, so every lane has the
-// same taps and consecutive LR columns. Dot products: each warp's partial goes to shared
-// memory; after the barrier every warp reads all partials of the cluster through
+//     p = r + beta p (band);  z = S B r + beta z (band + halo rows of r)
+// with two barriers. The adjoint pass for the 7x7 / x3 workload gives each lane s
+// consecutive columns, which together use every tap of a sampled row once (other extents:
+// lanes take columns of one residue mod s). Dot products: each warp's partial goes to
+// shared memory; after the barrier every warp reads all partials of the cluster through
 // distributed shared memory and sums them in one fixed order, so all CTAs hold identical
-// alpha and beta (no atomics). x, r, p, Ap stay in global memory (L2 resident), each CTA
-// touching only its band except for the halo rows of r.
+// alpha and beta (no atomics). When the band's x, r, p, Ap fit in shared memory they live
+// there and the halo rows of r are read from the neighbouring CTAs' shared memory, so an
+// iteration touches no global memory; otherwise they stay in global memory (L2 resident)
+// and every loop batches its loads.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -72,6 +74,7 @@ struct SrBand {
   const float *taps;     // kh * kw
   const int *rowmap;     // t -> z row index, or -1
   const int *lrow;       // z row index -> LR row
+  const int *zt;         // z row index -> its row-window entry t (HR row r0 - c1 + t)
   const int *colmap;     // c < W + kw - 1: LR column of wrapped HR column c - c2, or -1
   float *z;              // nz x lw
 };
@@ -122,35 +125,47 @@ __device__ __forceinline__ float row_taps(const float *ta, const float *row, int
   return acc;
 }
 
-// z (rows kept by the band) = S B v, or S B v + beta z when accumulate; v in global memory.
-template <int KH, int KW, int S>
-__device__ void band_sb(const SrBand &g, const float *__restrict__ v, float beta, bool accumulate) {
+// z (rows kept by the band) = S B v, or S B v + beta z when accumulate. rowp(k, li, a) gives
+// the row of v that tap row a of z row k (LR row li) reads: in global memory, or in the
+// band's halo-extended copy in shared memory.
+template <int KH, int KW, int S, class RowP>
+__device__ void band_sb(const SrBand &g, RowP &&rowp, float beta, bool accumulate) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SrDims<KH, KW, S> d(g);
   const int W = g.W, c1 = g.c1, c2 = g.c2;
+  constexpr int kRowsMax = KH > 0 ? KH : 1;
   for (int k = warp; k < g.nz; k += kSrWarps) {
     const int li = g.lrow[k];
     float *zr = g.z + (long)k * g.lw;
+    const float *rows[kRowsMax];
+    if constexpr (KH > 0) {
+#pragma unroll
+      for (int a = 0; a < KH; ++a) rows[a] = rowp(k, li, a);
+    }
     for (int j = lane; j < g.lw; j += 32) {
       const int w0 = d.s * j + c2;                 // HR column of tap b = 0
       const bool inner = (w0 - (d.kw - 1) >= 0) && (w0 <= W - 1);
       float acc = 0.f;
-      if (inner) {
-        if constexpr (KH > 0) {
+      if constexpr (KH > 0) {
+        if (inner) {
 #pragma unroll
-          for (int a = 0; a < KH; ++a)
-            acc = row_taps<KW>(g.taps + a * d.kw, v + (long)wrap1(d.s * li - a + c1, g.H) * W, w0,
-                               d.kw, acc);
+          for (int a = 0; a < KH; ++a) acc = row_taps<KW>(g.taps + a * d.kw, rows[a], w0, d.kw, acc);
         } else {
-          for (int a = 0; a < d.kh; ++a)
-            acc = row_taps<KW>(g.taps + a * d.kw, v + (long)wrap1(d.s * li - a + c1, g.H) * W, w0,
-                               d.kw, acc);
+#pragma unroll
+          for (int a = 0; a < KH; ++a) {
+            const float *ta = g.taps + a * d.kw;
+            for (int b = 0; b < d.kw; ++b) acc = fmaf(ta[b], rows[a][wrap1(w0 - b, W)], acc);
+          }
         }
       } else {
         for (int a = 0; a < d.kh; ++a) {
-          const float *row = v + (long)wrap1(d.s * li - a + c1, g.H) * W;
+          const float *row = rowp(k, li, a);
           const float *ta = g.taps + a * d.kw;
-          for (int b = 0; b < d.kw; ++b) acc = fmaf(ta[b], row[wrap1(w0 - b, W)], acc);
+          if (inner) {
+            acc = row_taps<KW>(ta, row, w0, d.kw, acc);
+          } else {
+            for (int b = 0; b < d.kw; ++b) acc = fmaf(ta[b], row[wrap1(w0 - b, W)], acc);
+          }
         }
       }
       zr[j] = accumulate ? fmaf(beta, zr[j], acc) : acc;
@@ -319,12 +334,12 @@ __device__ __forceinline__ void band_adjoint(const SrBand &g, Epi &&epi) {
     band_adjoint_residue<KH, KW, S>(g, epi);
 }
 
-// Shared memory (4-byte words): taps | rowmap | lrow | colmap | z | 2 x per-warp partials
-// | (resident bands only) x, r, p, Ap of the band. The caps are maxima over the launch's
+// Shared memory (4-byte words): taps | rowmap | lrow | zt | colmap | z | 2 x per-warp
+// partials | (resident bands only) x and r with kh - 1 halo rows on each side, p, Ap. The caps are maxima over the launch's
 // problems (sr_caps on the host). When the band's vectors do not fit (large images) they
 // stay in global memory and every loop batches its loads.
-template <int KH, int KW, int S>
-__global__ void __launch_bounds__(kSrThreads, 2)
+template <int KH, int KW, int S, int MINB>
+__global__ void __launch_bounds__(kSrThreads, MINB)
 k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, StepArgs sa,
           SrCaps caps, int resident) {
   extern __shared__ float sm_sr[];
@@ -349,13 +364,15 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   float *taps = sm_sr;
   int *rowmap = reinterpret_cast<int *>(taps + caps.taps);
   int *lrow = rowmap + caps.rows;
-  int *colmap = lrow + caps.zrows;
+  int *zt = lrow + caps.zrows;
+  int *colmap = zt + caps.zrows;
   g.z = reinterpret_cast<float *>(colmap + caps.cols);
   float *slot_a = g.z + caps.zfloats;
   float *slot_b = slot_a + kSrWarps;
   g.taps = taps;
   g.rowmap = rowmap;
   g.lrow = lrow;
+  g.zt = zt;
   g.colmap = colmap;
 
   for (int i = tid; i < g.kh * g.kw; i += kSrThreads) taps[i] = P->psf[i];
@@ -373,6 +390,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
     for (int t = 0; t < g.T; ++t)
       if (rowmap[t] >= 0) {
         lrow[nz] = rowmap[t];
+        zt[nz] = t;
         rowmap[t] = nz++;
       }
     nz_sh = nz;
@@ -383,14 +401,18 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   const float alpha = P->alpha, is2 = P->inv_sigma2;
   const long e0 = (long)g.r0 * g.W;
   const int nl = g.nb * g.W;                    // pixels of the band
-  float *r_g = P->cg_r;                         // r in global memory (halo rows for S B r)
+  float *r_g = P->cg_r;                         // r in global memory (non-resident bands)
+  const int hw = g.kh - 1;                      // halo rows of the resident copies of x, r
   // band vectors, indexed by the band-local pixel index
   float *xs, *rs, *ps, *aps;
+  float *xh = nullptr, *rh = nullptr;           // resident: [hw halo | band | hw halo] rows
   if (resident) {
-    xs = slot_b + kSrWarps;
-    rs = xs + caps.band;
-    ps = rs + caps.band;
+    xh = sm_sr + caps.resident_off;             // 16-byte aligned
+    rh = xh + caps.band_ext;
+    ps = rh + caps.band_ext;
     aps = ps + caps.band;
+    xs = xh + (long)hw * g.W;
+    rs = rh + (long)hw * g.W;
   } else {
     xs = P->cg_x + e0;
     rs = r_g + e0;
@@ -415,14 +437,67 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int l = l0 + u * kSrThreads;
-      if (l < nl) {
-        xs[l] = v[u];
-        P->cg_x[e0 + l] = v[u];
-      }
+      if (l < nl) xs[l] = v[u];
     }
   }
   cl.sync();
-  band_sb<KH, KW, S>(g, P->cg_x, 0.f, false);
+  // Rows of x or r read by S B: resident bands copy the hw rows above and below the band
+  // from the owning CTAs' shared memory (distributed shared memory) into their extended
+  // copy, which then holds HR row r0 - hw + t at row t, wrapped; otherwise global memory.
+  auto owner = [&](int R) {
+    int q = (int)((long)R * ncta / g.H);
+    while (q + 1 < ncta && (int)((long)(q + 1) * g.H / ncta) <= R) ++q;
+    while (q > 0 && (int)((long)q * g.H / ncta) > R) --q;
+    return q;
+  };
+  auto fill_halo = [&](float *ext, float *band_local) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int hr = warp; hr < 2 * hw; hr += kSrWarps) {
+      const int t = hr < hw ? hr : g.nb + hr;
+      const int R = wrap1(g.r0 - hw + t, g.H);
+      const int q = owner(R);
+      const float *src = cl.map_shared_rank(band_local, q) +
+                         (long)(R - (int)((long)q * g.H / ncta)) * g.W;
+      float *dst = ext + (long)t * g.W;
+      if ((g.W & 3) == 0) {   // rows start on 16-byte boundaries
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        const int n4 = g.W >> 2;
+        for (int c0 = lane; c0 < n4; c0 += 4 * 32) {
+          float4 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (c0 + 32 * u < n4) v[u] = s4[c0 + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (c0 + 32 * u < n4) d4[c0 + 32 * u] = v[u];
+        }
+      } else {
+        for (int c0 = lane; c0 < g.W; c0 += 8 * 32) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + 32 * u < g.W) v[u] = src[c0 + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + 32 * u < g.W) dst[c0 + 32 * u] = v[u];
+        }
+      }
+    }
+  };
+  auto x_row = [&](int k, int li, int a) -> const float * {
+    if (resident) return xh + (long)(zt[k] - a + hw) * g.W;
+    return P->cg_x + (long)wrap1(g.s * li - a + g.c1, g.H) * g.W;
+  };
+  auto r_row = [&](int k, int li, int a) -> const float * {
+    if (resident) return rh + (long)(zt[k] - a + hw) * g.W;
+    return r_g + (long)wrap1(g.s * li - a + g.c1, g.H) * g.W;
+  };
+  if (resident) {
+    fill_halo(xh, xs);
+    __syncthreads();
+  }
+  band_sb<KH, KW, S>(g, x_row, 0.f, false);
   __syncthreads();
   float dot = 0.f;
   // r = b - A x, p = r
@@ -430,12 +505,15 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
     const float ax = fmaf(acc, is2, alpha * xs[l]);
     const float rv = fmaf(alpha, f[e], b0[e]) - ax;
     rs[l] = rv;
-    if (resident) r_g[e] = rv;
     ps[l] = rv;
     dot = fmaf(rv, rv, dot);
   });
   float rr = cluster_total(cl, slot_b, dot, ncta);
-  band_sb<KH, KW, S>(g, r_g, 0.f, false);   // z = S B p, p = r
+  if (resident) {
+    fill_halo(rh, rs);
+    __syncthreads();
+  }
+  band_sb<KH, KW, S>(g, r_row, 0.f, false);   // z = S B p, p = r
   __syncthreads();
 
   for (int it = 0; it < P->cg_iters; ++it) {
@@ -470,7 +548,6 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
           xs[l] = fmaf(a, pv[u], xv[u]);
           const float rn = fmaf(-a, av[u], rv[u]);
           rs[l] = rn;
-          if (resident) r_g[e0 + l] = rn;
           dot = fmaf(rn, rn, dot);
         }
       }
@@ -494,7 +571,11 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
         if (l < nl) ps[l] = fmaf(beta, pv[u], rv[u]);
       }
     }
-    band_sb<KH, KW, S>(g, r_g, beta, true);   // z = S B r + beta z = S B p
+    if (resident) {
+      fill_halo(rh, rs);
+      __syncthreads();
+    }
+    band_sb<KH, KW, S>(g, r_row, beta, true);   // z = S B r + beta z = S B p
     __syncthreads();
   }
   cl.sync();   // every CTA has finished its remote reads of the last reduction's partials
@@ -655,20 +736,34 @@ void sr_caps(int H, int W, int scale, int kh, int kw, int ncta, SrCaps *c) {
       if (R % scale == 0 && R / scale < lh) ++nz;
     }
     o.rows = std::max(o.rows, T);
-    o.band = std::max(o.band, nb * W);
+    o.band = std::max(o.band, (nb * W + 3) & ~3);
+    o.band_ext = std::max(o.band_ext, ((nb + 2 * (kh - 1)) * W + 3) & ~3);
     o.zrows = std::max(o.zrows, nz);
     o.zfloats = std::max(o.zfloats, nz * lw);
   }
   *c = o;
 }
 
+static int sr_base_words(const SrCaps &c) {
+  return (c.taps + c.rows + 2 * c.zrows + c.cols + c.zfloats + 2 * kSrWarps + 3) & ~3;
+}
+
 int sr_smem_bytes(const SrCaps &c, int resident) {
-  return 4 * (c.taps + c.rows + c.zrows + c.cols + c.zfloats + 2 * kSrWarps +
-              (resident ? 4 * c.band : 0));
+  return 4 * (sr_base_words(c) + (resident ? 2 * c.band_ext + 2 * c.band : 0));
+}
+
+using SrKernel = void (*)(const ProbDev *, const int *, StepArgs, SrCaps, int);
+
+// The instantiations: 7x7 taps at scale 3 with the register budget of one or of two CTAs
+// per SM, and any extents.
+static SrKernel sr_kernel(int spec737, int minb) {
+  if (spec737) return minb == 1 ? k_sr_step<7, 7, 3, 1> : k_sr_step<7, 7, 3, 2>;
+  return k_sr_step<0, 0, 0, 2>;
 }
 
 cudaError_t sr_prepare(int cluster, int smem) {
-  for (const void *fn : {(const void *)k_sr_step<7, 7, 3>, (const void *)k_sr_step<0, 0, 0>}) {
+  for (const void *fn : {(const void *)k_sr_step<7, 7, 3, 1>, (const void *)k_sr_step<7, 7, 3, 2>,
+                         (const void *)k_sr_step<0, 0, 0, 2>}) {
     cudaError_t e = cudaSuccess;
     if (cluster > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
@@ -678,7 +773,7 @@ cudaError_t sr_prepare(int cluster, int smem) {
   return cudaSuccess;
 }
 
-int sr_max_active_clusters(int cluster, int smem) {
+int sr_max_active_clusters(int cluster, int smem, int spec737, int minb) {
   if (sr_prepare(cluster, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -695,7 +790,7 @@ int sr_max_active_clusters(int cluster, int smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_sr_step<0, 0, 0>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (const void *)sr_kernel(spec737, minb), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -706,6 +801,8 @@ cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_
                            const SrCaps &caps, StepArgs sa, cudaStream_t s) {
   if (n_sr <= 0) return cudaSuccess;
   if (cluster < 1 || cluster > kSrMaxCluster) return cudaErrorInvalidValue;
+  SrCaps c = caps;
+  c.resident_off = sr_base_words(caps);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_sr * cluster);
   cfg.blockDim = dim3(kSrThreads);
@@ -718,11 +815,8 @@ cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = caps.spec737
-                      ? cudaLaunchKernelEx(&cfg, k_sr_step<7, 7, 3>, d_probs, d_sr_probs, sa, caps,
-                                           caps.resident)
-                      : cudaLaunchKernelEx(&cfg, k_sr_step<0, 0, 0>, d_probs, d_sr_probs, sa, caps,
-                                           caps.resident);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, sr_kernel(caps.spec737, caps.minb), d_probs, d_sr_probs, sa,
+                                     c, caps.resident);
   count_launches(1);
   return e;
 }
