@@ -185,6 +185,51 @@ def ve_vs_fp_study(problems, Ps, torch, red):
             "rre_calls_to_fp200_cost_mean": float(np.mean(fill(need_cost)))}
 
 
+def secondary_workloads(red, torch, flush, steps=3, warmup=3):
+    """The other batched workloads, timed like the main one (device time, L2 flushed):
+    x3 super-resolution of nine 256x256 images with BF16 storage, and 64 uneven deblurring
+    problems (sides 128-512). Each step is one batched solve of 200 FP steps per problem."""
+    from paper_1805_02158_gb300 import synth
+    specs = [
+        ("sr256_bf16", "x3 SR 256x256 HR (85x85 LR) x9 images, Gaussian 7x7 std 1.6, noise 5, "
+                       "CG 20, NLM 5x5/11x11, RRE k=5, BF16 storage, 200 FP steps per solve",
+         [synth.sr_x3(i) for i in range(9)], {"storage": "bf16"}),
+        ("uneven64", "64 deblur problems, sides U{128,192,256,384,512}, uniform 9x9 or Gaussian "
+                     "std U[1,2] PSF, noise U[1,5], RRE k=5, 200 FP steps per solve",
+         [synth.batched_uneven(i) for i in range(64)], {}),
+    ]
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, desc, probs, kw in specs:
+        ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in probs]
+        x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in probs]
+        Ps = [red.Problem(red.config_for(p, ve="rre", ve_k=VE_K, **kw), y) for p, y in zip(probs, ys)]
+        B = red.Batch(Ps)
+        outs = [torch.empty_like(x) for x in x0s]
+        for _ in range(warmup):
+            B.solve(x0s, outs, CALLS, 0.0)
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.cuda.nvtx.range_push(f"timed_{name}")
+            B.solve(x0s, outs, CALLS, 0.0)
+            torch.cuda.nvtx.range_pop()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        pix = sum(p.height * p.width for p in probs)
+        total = float(sum(ms))
+        out[name] = {"workload": desc, "value": pix * CALLS * steps / (total / 1e3) / 1e6,
+                     "unit": UNIT, "ms_per_step": total / steps, "steps": steps, "warmup": warmup,
+                     "solves_per_s": len(probs) * steps / (total / 1e3),
+                     "launch_shapes": B.describe()}
+        del B, Ps
+    return out
+
+
 SERVE_RATE_HZ = 200.0
 SERVE_TOL = 1e-4
 SERVE_CAP = 300
@@ -256,6 +301,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving leg (0: skip it)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the SR and uneven-batch workloads")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -405,6 +452,9 @@ def main():
     study = None
     if not args.no_study and rank == 0:
         study = ve_vs_fp_study(problems, Ps, torch, red)
+    secondary = None
+    if not args.no_secondary and rank == 0:
+        secondary = secondary_workloads(red, torch, flush)
     serving = None
     if args.serve_requests > 0 and rank == 0:
         serving = serving_leg(red, args.serve_requests)
@@ -435,6 +485,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ve_vs_fp": study,
+        "other_workloads": secondary,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

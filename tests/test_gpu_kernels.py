@@ -118,6 +118,22 @@ def test_deblur_fp_step_both_fourier_paths(path, monkeypatch):
         assert rel_l2(to_host(out), ref) <= 1e-5
 
 
+def test_fourier_paths_agree(monkeypatch):
+    """The cluster solve (16 and 4 CTAs) and the three-pass solve agree to FP32 rounding on
+    the same input (same transforms, different partitions of the work)."""
+    torch = torch_cuda()
+    p = deblur_problem(96, 128, psf=synth.gaussian_psf(9, 1.6), seed=12)
+    outs = {}
+    for path in ("0", "4", "16"):
+        monkeypatch.setenv("RED_FFT_CLUSTER", path)
+        P = red.Problem(red.config_for(p), to_dev(p.y))
+        out = torch.empty((96, 128), device="cuda")
+        P.fp_step(to_dev(f32(p.y)), out)
+        outs[path] = to_host(out)
+    assert rel_l2(outs["4"], outs["16"]) <= 1e-6
+    assert rel_l2(outs["0"], outs["16"]) <= 1e-6
+
+
 def test_deblur_fp_step_large_uses_three_passes():
     """1024 x 1024 does not fit the cluster's shared memory: the three-pass path runs.
     Checked against the oracle's closed-form solve with f taken from the GPU denoiser
