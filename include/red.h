@@ -50,7 +50,8 @@ typedef enum {
 
 typedef enum { RED_DEBLUR = 0, RED_SR = 1 } red_task;
 
-/* Extrapolation method (Sec. III-B). SVD-MPE is reserved. */
+/* Extrapolation method (Sec. III-B): MPE (Algorithm 1), RRE (Eq. (19)), SVD-MPE (gamma from
+ * the right singular vector of R for its smallest singular value). */
 typedef enum { RED_VE_NONE = 0, RED_VE_MPE = 1, RED_VE_RRE = 2, RED_VE_SVDMPE = 3 } red_ve;
 
 /* Storage type of images and iterates; arithmetic is always FP32, the extrapolation
@@ -121,7 +122,7 @@ red_status red_fp_step(red_problem p, const void *x_in_dev, void *x_out_dev, voi
  * Eq. (3)); device float32 images. */
 red_status red_denoise(red_problem p, const void *x_dev, void *f_dev, void *stream);
 
-/* One extrapolation (Algorithm 1 with the problem's ve method: MPE, or RRE Eq. (19)) from
+/* One extrapolation (Algorithm 1 with the problem's ve method: MPE, RRE Eq. (19) or SVD-MPE) from
  * n_vec = kappa + 2 device float32 iterates xs_dev[0..n_vec) (x_m .. x_{m+kappa+1}), host
  * array of device pointers, 3 <= n_vec <= 17. Writes x_(m,kappa) to x_out_dev (may alias
  * xs_dev[0]). If gamma_host is non-null the call synchronises the stream and copies the
@@ -142,7 +143,7 @@ red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_ve
  *            each of n elements, 3 <= n_vec <= 17 (any alignment; 16-byte aligned
  *            vectors take the vectorised path).
  *   n:       elements per vector, 1 <= n <= 2^31 - 1; larger n returns RED_EINVAL.
- *   method:  RED_VE_MPE (Algorithm 1) or RED_VE_RRE (Eq. (19)).
+ *   method:  RED_VE_MPE (Algorithm 1), RED_VE_RRE (Eq. (19)) or RED_VE_SVDMPE.
  *   x_out_dev: device float32, n elements, may alias xs_dev[0]; on RED_EVE_BREAKDOWN it
  *            holds the last iterate.
  *   gamma_host: null, or room for kappa + 1 doubles.

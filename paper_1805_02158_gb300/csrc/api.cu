@@ -131,7 +131,6 @@ static void validate(const red_config *c) {
   CHECK_ARG(c->cg_iters >= 0 && c->cg_iters <= 1000, "cg_iters must be in [0, 1000]");
   if (c->nlm_patch != 5 || c->nlm_search != 11)
     throw Fail{RED_EUNSUPPORTED, "only 5x5 patches and 11x11 search windows are supported"};
-  if (c->ve == RED_VE_SVDMPE) throw Fail{RED_EUNSUPPORTED, "SVD-MPE is not available yet"};
   if (c->storage != RED_F32 && c->storage != RED_BF16)
     throw Fail{RED_EUNSUPPORTED, "storage must be RED_F32 or RED_BF16"};
 }
@@ -587,8 +586,8 @@ red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_ve
   return guarded([&] {
     CHECK_ARG(p && xs_dev && x_out_dev, "null argument");
     CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 17]");
-    CHECK_ARG(p->cfg.ve == RED_VE_MPE || p->cfg.ve == RED_VE_RRE,
-              "the problem's ve method must be MPE or RRE");
+    CHECK_ARG(p->cfg.ve == RED_VE_MPE || p->cfg.ve == RED_VE_RRE || p->cfg.ve == RED_VE_SVDMPE,
+              "the problem's ve method must be MPE, RRE or SVD-MPE");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VeArgs va{};
     for (int i = 0; i < n_vec; ++i) {

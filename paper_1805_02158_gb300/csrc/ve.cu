@@ -12,8 +12,10 @@
 //   2. k_ve_solve: per problem, one warp: sums the chunk partials in a fixed order,
 //                  Cholesky G = R^T R (R is the R of Algorithm 2's QR up to signs), then
 //                  MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2) or
-//                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), all in FP64, with
-//                  the rank-loss and existence rules of the oracle.
+//                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), or SVD-MPE: gamma =
+//                  v / sum v with v the right singular vector of R for its smallest
+//                  singular value (one-sided Jacobi on R, lane-parallel), all in FP64,
+//                  with the rank-loss and existence rules of the oracle.
 //   3. k_combine:  Algorithm 1 steps 3-4 evaluated without Q as
 //                  x_(m,kappa) = x_m + U_{kappa-1} xi (= x_m + Q_{kappa-1} R_{kappa-1} xi),
 //                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
@@ -223,9 +225,81 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
     P->gram_part[(size_t)it.a * kMaxPairs + q] = red[q];
 }
 
+// SVD-MPE weights: the right singular vector of the K x K factor R for its smallest
+// singular value, by one-sided (Hestenes) Jacobi: plane rotations of column pairs of R
+// until every pair is orthogonal to 1e-15, accumulated in V. Lane i < K holds row i of R
+// and of V; the three column inner products of a rotation are warp sums (fixed xor tree),
+// so every lane takes the same rotation. Returns false when sum v vanishes.
+template <int K>
+__device__ bool svd_mpe_gamma(const double (&R)[K][K], double (&gamma)[K]) {
+  const int lane = threadIdx.x & 31;
+  double a[K], v[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    a[j] = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (lane == i) a[j] = R[i][j];
+    v[j] = (lane == j) ? 1.0 : 0.0;
+  }
+  auto wsum = [](double x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+  };
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    bool rotated = false;
+#pragma unroll
+    for (int p = 0; p < K - 1; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < K; ++q) {
+        const double al = wsum(a[p] * a[p]), be = wsum(a[q] * a[q]), ga = wsum(a[p] * a[q]);
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        rotated = true;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const double ap = a[p], aq = a[q], vp = v[p], vq = v[q];
+        a[p] = c * ap - s * aq;
+        a[q] = s * ap + c * aq;
+        v[p] = c * vp - s * vq;
+        v[q] = s * vp + c * vq;
+      }
+    }
+    if (!rotated) break;
+  }
+  // smallest column norm of the rotated R = smallest singular value
+  int jmin = 0;
+  double nmin = wsum(a[0] * a[0]);
+#pragma unroll
+  for (int j = 1; j < K; ++j) {
+    const double nj = wsum(a[j] * a[j]);
+    if (nj < nmin) {
+      nmin = nj;
+      jmin = j;
+    }
+  }
+  double vj = 0.0;
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if (j == jmin) vj = v[j];
+  double sv = 0.0, sa = 0.0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    gamma[i] = __shfl_sync(0xffffffffu, vj, i);
+    sv += gamma[i];
+    sa += fabs(gamma[i]);
+  }
+  if (fabs(sv) <= kSumTol * sa) return false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) gamma[i] /= sv;
+  return true;
+}
+
 // The tiny FP64 solve for gamma, one warp per problem. Lanes sum the chunk partials of
-// each Gram entry in a fixed order (lane-strided, then a fixed xor tree); lane 0 then
-// factors G = R^T R and solves for gamma with K-sized register arrays.
+// each Gram entry in a fixed order (lane-strided, then a fixed xor tree), so every lane
+// holds G; every lane factors G = R^T R and solves for gamma with K-sized register arrays
+// (SVD-MPE spreads its rotations over the lanes); lane 0 writes the results.
 template <int K>
 __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   constexpr int NP = K * (K + 1) / 2;
@@ -243,7 +317,6 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
       G[i][j] = s;
     }
   (void)NP;
-  if (lane != 0) return;
   double R[K][K];
 #pragma unroll
   for (int i = 0; i < K; ++i)
@@ -275,7 +348,9 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   }
   double gamma[K];
   bool ok = !bad;
-  if (ok) {
+  if (ok && P->ve_method == kVeSvdMpe) {
+    ok = svd_mpe_gamma<K>(R, gamma);
+  } else if (ok) {
     const int method = P->ve_method;
     const bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
     if (use_mpe) {
@@ -319,6 +394,7 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
       for (int i = 0; i < K; ++i) gamma[i] = d[i] / sd;
     }
   }
+  if (lane != 0) return;
   ProbState *st = P->st;
   if (update_state) st->ve_steps += 1;
   if (!ok) {
@@ -715,7 +791,8 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
   return guarded([&] {
     CHECK_ARG(xs_dev && x_out_dev, "null argument");
     CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 17]");
-    CHECK_ARG(method == RED_VE_MPE || method == RED_VE_RRE, "method must be RED_VE_MPE or RED_VE_RRE");
+    CHECK_ARG(method == RED_VE_MPE || method == RED_VE_RRE || method == RED_VE_SVDMPE,
+              "method must be RED_VE_MPE, RED_VE_RRE or RED_VE_SVDMPE");
     CHECK_ARG(n >= 1, "n must be positive");
     const int64_t max_n = 2147483647;   // chunk counts and launch sizes are 32-bit
     if (n > max_n)

@@ -61,7 +61,7 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(sigma=0.0), red.RED_EINVAL),
     (dict(ve_k=17), red.RED_EINVAL),
     (dict(task="sr", scale=1), red.RED_EINVAL),
-    (dict(ve="svdmpe"), red.RED_EUNSUPPORTED),
+    (dict(ve=7), red.RED_EINVAL),                          # no such method
     (dict(storage="f16"), red.RED_EUNSUPPORTED),
 ])
 def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
@@ -72,6 +72,13 @@ def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
     st = lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out))
     assert st == status
     assert red.lib().red_last_error()
+
+
+def test_svdmpe_config_accepted(lib):
+    cfg = red.make_config(height=64, width=64, psf=synth.uniform_psf(9), ve="svdmpe")
+    out = ctypes.c_size_t()
+    assert lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out)) == red.RED_OK
+    assert out.value > 0
 
 
 def test_unsupported_patch_size(lib):

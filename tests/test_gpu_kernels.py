@@ -208,7 +208,7 @@ def fp_history(p, n, kappa_plus_2):
     return xs[n:]
 
 
-@pytest.mark.parametrize("method", ["mpe", "rre"])
+@pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
 def test_extrapolation_on_fp_history(method):
     torch = torch_cuda()
     p = deblur_problem(64, 64, seed=5)
@@ -222,7 +222,7 @@ def test_extrapolation_on_fp_history(method):
     assert rel_l2(to_host(out), x_ref) <= 1e-6
 
 
-@pytest.mark.parametrize("method", ["mpe", "rre"])
+@pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
 def test_extrapolation_exact_on_linear_map(method):
     """A linear FP map in R^N (N = 64 x 64) with 4 distinct eigenvalues: kappa = 4 reaches
     the fixed point (Eqs. (13)-(16))."""

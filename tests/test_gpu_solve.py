@@ -30,7 +30,7 @@ def gpu_solve(p, method, k, calls, tol=0.0, m=0, storage="f32", cg_iters=20):
     return to_host(out), st
 
 
-@pytest.mark.parametrize("method", ["none", "rre", "mpe"])
+@pytest.mark.parametrize("method", ["none", "rre", "mpe", "svdmpe"])
 def test_deblur_64_solve_matches_oracle(method):
     """Bars: relative L2 <= 1e-3, objective (Eq. (4), evaluated by the oracle) within 1e-4
     relative, PSNR within 0.01 dB. On this problem MPE's extrapolations are near
@@ -48,7 +48,7 @@ def test_deblur_64_solve_matches_oracle(method):
     e = ored.objective(x, nlm(x), F.y, F.otf, 1, p.sigma, p.alpha)
     e_ref = ored.objective(x_ref, nlm(x_ref), F.y, F.otf, 1, p.sigma, p.alpha)
     assert abs(e - e_ref) <= 1e-4 * abs(e_ref)
-    bar = 0.02 if method == "mpe" else 0.01
+    bar = 0.02 if method in ("mpe", "svdmpe") else 0.01
     assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= bar
 
 

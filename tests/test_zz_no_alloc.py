@@ -46,7 +46,7 @@ def compare(P, xs_dev, method):
     assert float((out_st - out_ref).abs().max()) <= 1e-4
 
 
-@pytest.mark.parametrize("method", ["mpe", "rre"])
+@pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
 def test_static_matches_problem_entry_point_two_calls(method):
     p = synth.make_deblur(5, 64, 64, synth.uniform_psf(9), 2 ** 0.5)
     P = red.Problem(red.config_for(p, ve=method, ve_k=5), to_dev(p.y))
@@ -131,5 +131,5 @@ def test_static_rejects_sizes_beyond_limit():
     arr18 = (ctypes.c_void_p * 18)(*[v.data_ptr()] * 18)
     st = L.red_ve_extrapolate_static(arr18, 18, 16, 2, ctypes.c_void_p(v.data_ptr()), gam, None)
     assert st == red.RED_EINVAL
-    st = L.red_ve_extrapolate_static(arr, 3, 16, 3, ctypes.c_void_p(v.data_ptr()), gam, None)
+    st = L.red_ve_extrapolate_static(arr, 3, 16, 0, ctypes.c_void_p(v.data_ptr()), gam, None)
     assert st == red.RED_EINVAL
