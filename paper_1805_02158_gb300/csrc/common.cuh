@@ -12,7 +12,7 @@ namespace red {
 constexpr int kMaxK = 16;                       // largest ve_k (columns of U)
 constexpr int kMaxPairs = kMaxK * (kMaxK + 1) / 2;
 constexpr int kGramChunk = 2048;                // pixels per Gram / combine work unit
-constexpr int kNlmR = 8;                        // output rows per NLM thread
+constexpr int kNlmR = 6;                        // output rows per NLM thread
 constexpr int kNlmTW = 60;                      // output columns per NLM warp (64 - 4 halo)
 constexpr double kRankTol = 1e-12;              // rank-loss threshold on r_jj^2 / ||u_j||^2
 constexpr double kSumTol = 1e-12;               // MPE existence: |sum c| > tol * sum |c|

@@ -6,12 +6,12 @@
 //   w(p,d) = exp(-(1/(25 h^2)) sum_{t in [-2,2]^2} (xp(p+t) - xp(p+d+t))^2),
 // xp = x extended by half-sample symmetric reflection.
 //
-// GB300 mapping. One warp = a tile of 60 output columns x 8 output rows (warp-sized work
+// GB300 mapping. One warp = a tile of 60 output columns x kNlmR = 6 output rows (warp-sized work
 // units balance evenly over the SMs; a CTA is 1-4 independent warps); the tile plus a
 // 7-pixel halo (search radius 5 + patch radius 2) is staged once in shared memory, prescaled by k = sqrt(log2(e) / (25 h^2)) so that a weight is a single
-// ex2.approx of a negated patch distance. Each lane owns 2 adjacent columns and 8 rows:
+// ex2.approx of a negated patch distance. Each lane owns 2 adjacent columns and kNlmR rows:
 //   * the lane's own patch rows a(rr) (12 x 2 values) stay in registers for all 121 offsets;
-//   * for each dx the lane loads the 22 candidate rows it needs for all 11 dy once, so
+//   * for each dx the lane loads the kNlmR + 14 candidate rows it needs for all 11 dy once, so
 //     the dy loop (fully unrolled) only renames registers;
 //   * vertical 5-row sums of squared differences slide down the column with 2 FMAs/row;
 //   * horizontal 5-column sums use 4 warp shuffles per row (the warp covers 64 columns
@@ -19,7 +19,7 @@
 // Per output pixel and offset: ~8.4 FP32 ops, 1 MUFU.EX2, 2 SHFL; no shared-memory
 // traffic in the inner loop beyond one candidate row per dy.
 //
-// Work decomposition is fixed to an (8-row, 2-column) grid in image coordinates, so a
+// Work decomposition is fixed to a (kNlmR-row, 2-column) grid in image coordinates, so a
 // pixel's arithmetic (and result, bit for bit) does not depend on the CTA shape chosen
 // by the autotuner or on which other problems share the launch.
 #include "common.cuh"
