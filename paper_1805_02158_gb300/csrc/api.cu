@@ -172,8 +172,9 @@ int sr_cluster_override() {
   return (v == 8 || v == 16) ? v : -1;
 }
 
-void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
-  release();
+void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStream_t stream,
+                 bool async) {
+  if (!async) release();
   lc = cfg;
   if (lc.fft_cluster > 0 && !cluster_ok(lc.fft_cluster)) lc.fft_cluster = 0;
   std::vector<Item> nlm, rows, cols, chunks;
@@ -233,12 +234,24 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
   all.insert(all.end(), rows.begin(), rows.end());
   all.insert(all.end(), cols.begin(), cols.end());
   all.insert(all.end(), chunks.begin(), chunks.end());
-  CUDA_OK(cudaMalloc(&d_items, sizeof(Item) * std::max<size_t>(1, all.size())));
-  CUDA_OK(cudaMemcpy(d_items, all.data(), sizeof(Item) * all.size(), cudaMemcpyHostToDevice));
-  if (n_sr) {
-    CUDA_OK(cudaMalloc(&d_sr, sizeof(int) * n_sr));
-    CUDA_OK(cudaMemcpy(d_sr, sr.data(), sizeof(int) * n_sr, cudaMemcpyHostToDevice));
-  }
+  // device lists: grown when needed, uploaded synchronously or in stream order
+  auto upload = [&](auto *&dev, size_t &cap, const auto &host) {
+    using T = typename std::decay<decltype(host[0])>::type;
+    const size_t n = std::max<size_t>(1, host.size());
+    if (!dev || cap < n) {
+      if (dev) cudaFree(dev);
+      dev = nullptr;
+      CUDA_OK(cudaMalloc(&dev, sizeof(T) * n));
+      cap = n;
+    }
+    if (host.empty()) return;
+    if (async)
+      CUDA_OK(cudaMemcpyAsync(dev, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice, stream));
+    else
+      CUDA_OK(cudaMemcpy(dev, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice));
+  };
+  upload(d_items, items_cap, all);
+  if (n_sr) upload(d_sr, sr_cap_n, sr);
   sr_cap = SrCaps{};
   if (n_sr) {
     // shared memory of the CG kernel grows with the band height: wide images need the
@@ -283,10 +296,7 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg) {
       sr_cap.minb = 1;
   }
   n_fused = (int)fused.size();
-  if (n_fused) {
-    CUDA_OK(cudaMalloc(&d_fused, sizeof(int) * n_fused));
-    CUDA_OK(cudaMemcpy(d_fused, fused.data(), sizeof(int) * n_fused, cudaMemcpyHostToDevice));
-  }
+  if (n_fused) upload(d_fused, fused_cap, fused);
 }
 
 void prepare_launch_attrs(const Plan &pl) {
@@ -305,6 +315,7 @@ void Plan::release() {
   d_items = nullptr;
   d_sr = nullptr;
   d_fused = nullptr;
+  items_cap = sr_cap_n = fused_cap = 0;
   n_fused = 0;
 }
 

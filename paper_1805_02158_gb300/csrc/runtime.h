@@ -68,7 +68,11 @@ struct Plan {
   int row_tw_cap = 0, row_buf_cap = 0, col_tw_cap = 0, col_buf_cap = 0;
   SrCaps sr_cap;              // shared-memory extents of the super-resolution CG launch
   std::vector<int> n_row_items;
-  void build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg);
+  // Device lists are reused when large enough; with a stream the uploads are ordered on it
+  // (no device-wide synchronisation), otherwise they are synchronous.
+  size_t items_cap = 0, sr_cap_n = 0, fused_cap = 0;
+  void build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStream_t stream = nullptr,
+             bool async = false);
   void release();
   ~Plan() { release(); }
 };

@@ -1,21 +1,25 @@
 // Serving loop: continuous batching of RED solves (Algorithm 3 per request) of different
 // sizes and tasks, admitted by device-memory footprint.
 //
-// One scheduler thread owns the GPU work. Each tick it
+// One scheduler thread owns the GPU work. Requests are grouped by task and extrapolation
+// settings (ve, ve_k, ve_m); every group has its own stream and advances one cycle of
+// Algorithm 3 at a time, independently of the other groups, so a deblurring group is not
+// held back by the slower super-resolution CG of another. The loop
 //   1. admits waiting requests (FIFO) while a slot is free and the request's device
 //      footprint fits in the budget: it takes an idle problem of the same shape and
 //      physics from the pool (or creates one), uploads y, recomputes the constants,
 //      writes x0 into ring slot 0 and arms the request's termination state;
-//   2. runs one cycle of Algorithm 3 (ve_m + ve_k FP steps and one extrapolation) for
-//      every running request at once, one launch per phase per group of requests that
-//      share (ve, ve_k, ve_m); requests that meet rel_tol or their budget inside the
-//      cycle stop there, on the device;
-//   3. reads the termination states back (one small copy), returns finished results to
-//      host memory and puts their problems back in the pool, freeing the slot.
-// Every running request starts each cycle from ring slot 0, so newly admitted and
-// running requests share the same launches. A request's arithmetic never depends on the
-// other requests in flight (fixed per-problem work decomposition, no cross-problem
-// reductions), so its result is the same alone and in the mix.
+//   2. for every group whose cycle in flight has completed: reads the termination states
+//      (copied back at the end of the cycle), returns finished results to host memory
+//      and puts their problems back in the pool, freeing the slot;
+//   3. for every idle group with running requests (new ones included): launches one
+//      cycle (ve_m + ve_k FP steps and one extrapolation; one launch per phase over the
+//      group's requests; requests that meet rel_tol or their budget stop on the device)
+//      and the copy of the termination states, then records the group's event.
+// Every running request starts each cycle from ring slot 0, so newly admitted and running
+// requests share the same launches. A request's arithmetic never depends on the other
+// requests in flight (fixed per-problem work decomposition, no cross-problem reductions),
+// so its result is the same alone and in the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,7 +80,7 @@ std::string key_of(const red_config &c, const std::vector<float> &psf) {
 
 std::string group_of(const red_config &c) {
   std::ostringstream o;
-  o << c.ve << "|" << c.ve_k << "|" << c.ve_m;
+  o << c.task << "|" << c.ve << "|" << c.ve_k << "|" << c.ve_m;
   return o.str();
 }
 
@@ -99,18 +103,23 @@ struct red_server_s {
   std::map<std::string, std::vector<red_problem_s *>> pool;
   std::map<std::string, size_t> pool_bytes;
   std::vector<std::shared_ptr<Request>> running;
-  struct Group {                                         // launch tables of one group
-    std::vector<red_problem_s *> members;                // as of the last build
+  struct Group {                                         // requests sharing launches
+    int ve = 0, k = 1, m = 0;
+    std::vector<red_problem_s *> members;                // as of the last table build
     red::Plan plan;
+    std::vector<red::ProbDev> pds;
     red::ProbDev *d_pds = nullptr;
     int pds_cap = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;                          // end of the cycle in flight
+    bool busy = false;
+    std::vector<std::shared_ptr<Request>> inflight;      // requests of that cycle
+    ProbState *h_states = nullptr;                       // pinned, one per inflight request
+    int states_cap = 0;
   };
   std::map<std::string, std::unique_ptr<Group>> groups;
   float *d_stage = nullptr;                              // y / x0 staging (largest image)
   size_t stage_elems = 0;
-  ProbState *h_states = nullptr;
-  ProbState *d_states = nullptr;
-  int states_cap = 0;
   std::string sticky_error;
 };
 
@@ -213,29 +222,35 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   r->t_admit = Clock::now();
 }
 
-// One cycle of Algorithm 3 for the running requests of one group. The work lists and
-// descriptor table are rebuilt only when the group's membership changed.
-void run_group_cycle(red_server_s *S, red_server_s::Group &g,
-                     const std::vector<red_problem_s *> &members, int ve, int k, int m) {
-  cudaStream_t s = S->stream;
+// Launches one cycle of Algorithm 3 for the group's running requests on the group's
+// stream, then the copy of their termination states and the group's event. The work
+// lists and descriptor table are rebuilt (in stream order, buffers reused) only when the
+// membership changed.
+void launch_group_cycle(red_server_s::Group &g, std::vector<std::shared_ptr<Request>> members) {
+  cudaStream_t s = g.stream;
   const int n = (int)members.size();
-  if (members != g.members) {
-    std::vector<ProbDev> pds;
-    for (auto *p : members) pds.push_back(p->pd);   // st = the problem's own state
+  std::vector<red_problem_s *> probs;
+  for (auto &r : members) probs.push_back(r->prob);
+  if (probs != g.members) {
+    g.pds.clear();
+    for (auto *p : probs) g.pds.push_back(p->pd);   // st = the problem's own state
+    // fixed launch shapes, so that a request's arithmetic (its reduction orders included)
+    // does not depend on which other requests share the launches
     LaunchCfg lc;
-    g.plan.build(pds, lc);
-    for (int i = 0; i < n; ++i) pds[i].n_row_items = g.plan.n_row_items[i];
+    lc.sr_cluster = 16;
+    g.plan.build(g.pds, lc, s, true);
+    for (int i = 0; i < n; ++i) g.pds[i].n_row_items = g.plan.n_row_items[i];
     if (n > g.pds_cap) {
       if (g.d_pds) cudaFree(g.d_pds);
       g.d_pds = nullptr;
       CUDA_OK(cudaMalloc(&g.d_pds, sizeof(ProbDev) * n));
       g.pds_cap = n;
     }
-    CUDA_OK(cudaMemcpy(g.d_pds, pds.data(), sizeof(ProbDev) * n, cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpyAsync(g.d_pds, g.pds.data(), sizeof(ProbDev) * n, cudaMemcpyHostToDevice, s));
     prepare_launch_attrs(g.plan);
-    g.members = members;
+    g.members = probs;
   }
-  for (const CycleOp &op : cycle_ops(ve, k, m)) {
+  for (const CycleOp &op : cycle_ops(g.ve, g.k, g.m)) {
     if (op.kind == 0) {
       StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
       launch_fp_step(g.d_pds, g.plan, sa, 0, s);
@@ -248,14 +263,76 @@ void run_group_cycle(red_server_s *S, red_server_s::Group &g,
       launch_ve(g.d_pds, n, g.plan, va, s);
     }
   }
+  if (n > g.states_cap) {
+    if (g.h_states) cudaFreeHost(g.h_states);
+    g.h_states = nullptr;
+    CUDA_OK(cudaMallocHost(&g.h_states, sizeof(ProbState) * n));
+    g.states_cap = n;
+  }
+  for (int i = 0; i < n; ++i) {
+    red_problem_s *P = probs[i];
+    CUDA_OK(cudaMemcpyAsync(g.h_states + i, static_cast<char *>(P->block) + P->L.state,
+                            sizeof(ProbState), cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_OK(cudaEventRecord(g.done, s));
+  g.inflight = std::move(members);
+  g.busy = true;
+}
+
+// The group's cycle has completed: finished requests get their result and release their
+// slot; the others stay running.
+void complete_group_cycle(red_server_s *S, red_server_s::Group &g) {
+  g.busy = false;
+  std::vector<std::shared_ptr<Request>> done;
+  for (size_t i = 0; i < g.inflight.size(); ++i) {
+    auto &r = g.inflight[i];
+    const ProbState &st = g.h_states[i];
+    if (!st.done) continue;
+    red_problem_s *P = r->prob;
+    CUDA_OK(launch_fetch_slot(P->d_pd, st.final_slot,
+                              reinterpret_cast<float *>(static_cast<char *>(P->block) + P->L.tmp),
+                              g.stream));
+    CUDA_OK(cudaMemcpyAsync(r->x_out, static_cast<char *>(P->block) + P->L.tmp,
+                            (size_t)P->pd.N * 4, cudaMemcpyDeviceToHost, g.stream));
+    CUDA_OK(cudaStreamSynchronize(g.stream));
+    r->stats.fp_calls = st.calls;
+    r->stats.ve_steps = st.ve_steps;
+    r->stats.ve_breakdowns = st.ve_breakdowns;
+    r->stats.converged = st.converged;
+    r->stats.rel_change = st.rel_change;
+    r->stats.sum_abs_gamma = st.sum_abs_gamma;
+    done.push_back(r);
+  }
+  g.inflight.clear();
+  for (auto &r : done) {
+    S->pool[r->key].push_back(r->prob);
+    r->prob = nullptr;
+    S->running.erase(std::find(S->running.begin(), S->running.end(), r));
+    finish(S, r, (r->tol > 0.0 && !r->stats.converged) ? RED_ENOT_CONVERGED : RED_OK);
+  }
 }
 
 void release_group(red_server_s::Group &g) {
+  if (g.stream) cudaStreamSynchronize(g.stream);
   g.plan.release();
   if (g.d_pds) cudaFree(g.d_pds);
-  g.d_pds = nullptr;
-  g.pds_cap = 0;
-  g.members.clear();
+  if (g.h_states) cudaFreeHost(g.h_states);
+  if (g.done) cudaEventDestroy(g.done);
+  if (g.stream) cudaStreamDestroy(g.stream);
+  g = red_server_s::Group();
+}
+
+red_server_s::Group &group_for(red_server_s *S, const Request &r) {
+  auto &g = S->groups[r.group];
+  if (!g) {
+    g.reset(new red_server_s::Group());
+    g->ve = r.cfg.ve;
+    g->k = r.cfg.ve_k;
+    g->m = r.cfg.ve_m;
+    CUDA_OK(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
+  }
+  return *g;
 }
 
 void scheduler(red_server_s *S) {
@@ -296,76 +373,45 @@ void scheduler(red_server_s *S) {
         to_admit.push_back(r);
       }
     }
-    for (auto &r : to_admit) {
-      try {
-        admit(S, r);
-        S->running.push_back(r);
-      } catch (const Fail &e) {
-        if (r->prob) {   // a pooled problem whose observation upload failed
-          S->used -= S->pool_bytes[r->key];
-          delete r->prob;
-          r->prob = nullptr;
-        }
-        r->stats = red_stats{};
-        finish(S, r, e.st);
-      }
-    }
-    if (S->running.empty()) continue;
+    bool progressed = !to_admit.empty();
     try {
-      std::map<std::string, std::vector<red_problem_s *>> groups;
-      std::map<std::string, const red_config *> gcfg;
-      for (auto &r : S->running) {
-        groups[r->group].push_back(r->prob);
-        gcfg[r->group] = &r->cfg;
-      }
-      for (auto &kv : groups) {
-        const red_config *c = gcfg[kv.first];
-        auto &g = S->groups[kv.first];
-        if (!g) g.reset(new red_server_s::Group());
-        run_group_cycle(S, *g, kv.second, c->ve, c->ve_k, c->ve_m);
-      }
-      // termination states
-      const int n = (int)S->running.size();
-      if (n > S->states_cap) {
-        if (S->h_states) cudaFreeHost(S->h_states);
-        S->h_states = nullptr;
-        CUDA_OK(cudaMallocHost(&S->h_states, sizeof(ProbState) * n));
-        S->states_cap = n;
-      }
-      for (int i = 0; i < n; ++i) {
-        red_problem_s *P = S->running[i]->prob;
-        CUDA_OK(cudaMemcpyAsync(S->h_states + i, static_cast<char *>(P->block) + P->L.state,
-                                sizeof(ProbState), cudaMemcpyDeviceToHost, S->stream));
-      }
-      CUDA_OK(cudaStreamSynchronize(S->stream));
-      std::vector<std::shared_ptr<Request>> still;
-      for (int i = 0; i < n; ++i) {
-        auto &r = S->running[i];
-        const ProbState &st = S->h_states[i];
-        if (!st.done) {
-          still.push_back(r);
-          continue;
+      for (auto &r : to_admit) {
+        try {
+          admit(S, r);
+          S->running.push_back(r);
+        } catch (const Fail &e) {
+          if (r->prob) {   // a pooled problem whose observation upload failed
+            S->used -= S->pool_bytes[r->key];
+            delete r->prob;
+            r->prob = nullptr;
+          }
+          r->stats = red_stats{};
+          finish(S, r, e.st);
         }
-        red_problem_s *P = r->prob;
-        CUDA_OK(launch_fetch_slot(P->d_pd, st.final_slot,
-                                  reinterpret_cast<float *>(static_cast<char *>(P->block) + P->L.tmp),
-                                  S->stream));
-        CUDA_OK(cudaMemcpyAsync(r->x_out, static_cast<char *>(P->block) + P->L.tmp,
-                                (size_t)P->pd.N * 4, cudaMemcpyDeviceToHost, S->stream));
-        CUDA_OK(cudaStreamSynchronize(S->stream));
-        r->stats.fp_calls = st.calls;
-        r->stats.ve_steps = st.ve_steps;
-        r->stats.ve_breakdowns = st.ve_breakdowns;
-        r->stats.converged = st.converged;
-        r->stats.rel_change = st.rel_change;
-        r->stats.sum_abs_gamma = st.sum_abs_gamma;
-        S->pool[r->key].push_back(P);
-        r->prob = nullptr;
-        finish(S, r, (r->tol > 0.0 && !st.converged) ? RED_ENOT_CONVERGED : RED_OK);
       }
-      S->running.swap(still);
+      // completed cycles
+      for (auto &kv : S->groups) {
+        auto &g = *kv.second;
+        if (!g.busy) continue;
+        const cudaError_t q = cudaEventQuery(g.done);
+        if (q == cudaErrorNotReady) continue;
+        CUDA_OK(q);
+        complete_group_cycle(S, g);
+        progressed = true;
+      }
+      // next cycles of idle groups (newly admitted requests join here)
+      std::map<std::string, std::vector<std::shared_ptr<Request>>> members;
+      for (auto &r : S->running) members[r->group].push_back(r);
+      for (auto &kv : members) {
+        auto &g = group_for(S, *kv.second.front());
+        if (g.busy) continue;
+        launch_group_cycle(g, kv.second);
+        progressed = true;
+      }
     } catch (const Fail &e) {
       S->sticky_error = e.msg;
+      for (auto &kv : S->groups)
+        if (kv.second->stream) cudaStreamSynchronize(kv.second->stream);
       for (auto &r : S->running) {
         if (r->prob) {
           delete r->prob;
@@ -379,7 +425,10 @@ void scheduler(red_server_s *S) {
         for (auto *p : kv.second) delete p;
       S->pool.clear();
       for (auto &kv : S->groups) release_group(*kv.second);
+      S->groups.clear();
+      continue;
     }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
@@ -483,7 +532,6 @@ red_status red_server_destroy(red_server s) {
       for (auto *p : kv.second) delete p;
     for (auto &kv : s->groups) release_group(*kv.second);
     if (s->d_stage) cudaFree(s->d_stage);
-    if (s->h_states) cudaFreeHost(s->h_states);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return RED_OK;
