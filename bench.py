@@ -272,12 +272,17 @@ def serving_leg(red, n_req, budget_gb=32, slots=32):
             if wait > 0:
                 time.sleep(wait)
             tickets.append(S.submit(cfgs[i], r["y"], outs[i], SERVE_CAP, SERVE_TOL))
-        stats = []
+        stats, statuses = [], []
         for t in tickets:
             st, s = S.wait(t, -1)
             stats.append(s)
+            statuses.append(st)
         wall = time.perf_counter() - t0
         S.close()
+        bad = [st for st in statuses if st not in (red.RED_OK, red.RED_ENOT_CONVERGED)]
+        if bad:
+            raise RuntimeError(f"serving: {len(bad)} requests failed "
+                               f"({red.status_string(bad[0])}: {red.lib().red_last_error()})")
         lat = np.array([s["ms_total"] for s in stats])
         calls = np.array([s["fp_calls"] for s in stats])
         pix = np.array([r["height"] * r["width"] for r in reqs])

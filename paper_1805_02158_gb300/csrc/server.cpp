@@ -1,8 +1,8 @@
 // Serving loop: continuous batching of RED solves (Algorithm 3 per request) of different
 // sizes and tasks, admitted by device-memory footprint.
 //
-// One scheduler thread owns the GPU work. Requests are grouped by task and extrapolation
-// settings (ve, ve_k, ve_m); every group has its own stream and advances one cycle of
+// One scheduler thread owns the GPU work. Requests are grouped by task, size class and
+// extrapolation settings (ve, ve_k, ve_m); every group has its own stream and advances one cycle of
 // Algorithm 3 at a time, independently of the other groups, so a deblurring group is not
 // held back by the slower super-resolution CG of another. The loop
 //   1. admits waiting requests (FIFO) while a slot is free and the request's device
@@ -78,9 +78,13 @@ std::string key_of(const red_config &c, const std::vector<float> &psf) {
   return o.str();
 }
 
+// Requests of one task, extrapolation setting and size class share launches; small images
+// are not paced by the FP steps of large ones (classes: up to 256^2, up to 512^2, larger).
 std::string group_of(const red_config &c) {
+  const long n = (long)c.height * c.width;
+  const int size_class = n <= 256L * 256 ? 0 : (n <= 512L * 512 ? 1 : 2);
   std::ostringstream o;
-  o << c.task << "|" << c.ve << "|" << c.ve_k << "|" << c.ve_m;
+  o << c.task << "|" << size_class << "|" << c.ve << "|" << c.ve_k << "|" << c.ve_m;
   return o.str();
 }
 

@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -761,15 +762,24 @@ static SrKernel sr_kernel(int spec737, int minb) {
   return k_sr_step<0, 0, 0, 2>;
 }
 
+// The dynamic shared-memory limit of a kernel only ever grows (high-water mark): launches
+// of other problem sets, possibly still in flight on other streams, keep their room.
 cudaError_t sr_prepare(int cluster, int smem) {
+  static std::mutex mu;
+  static int high_water = 0;
+  static bool non_portable = false;
+  std::lock_guard<std::mutex> lk(mu);
   for (const void *fn : {(const void *)k_sr_step<7, 7, 3, 1>, (const void *)k_sr_step<7, 7, 3, 2>,
                          (const void *)k_sr_step<0, 0, 0, 2>}) {
     cudaError_t e = cudaSuccess;
-    if (cluster > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(smem, 1));
+    if (cluster > 8 && !non_portable)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && smem > high_water)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
+  if (cluster > 8) non_portable = true;
+  high_water = std::max(high_water, smem);
   return cudaSuccess;
 }
 

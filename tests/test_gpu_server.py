@@ -68,6 +68,19 @@ def test_server_alone_equals_mix():
     assert np.array_equal(alone0[0], mix[0])
 
 
+def test_server_groups_of_different_sizes_run_concurrently():
+    """Requests of both tasks in several size classes (separate groups, streams and
+    shared-memory footprints) all complete, and one of them equals its solve alone."""
+    probs = [synth.sr_x3(40, 96), synth.sr_x3(41, 384), synth.deblur_gauss256(42, 128),
+             synth.deblur_gauss256(43, 384), synth.sr_x3(44, 96), synth.deblur_gauss256(45, 768)]
+    mix, stats = serve(probs, calls=20)
+    assert all(s["fp_calls"] == 20 for s in stats)
+    alone, _ = serve([probs[1]], calls=20)
+    assert np.array_equal(alone[0], mix[1])
+    for p, out in zip(probs, mix):
+        assert np.isfinite(out).all()
+
+
 def test_server_admission_under_tight_budget():
     """Budget for one 128x128 problem: requests of distinct shapes run one after the
     other (idle problems are freed to make room) and give the same results."""
