@@ -203,21 +203,32 @@ __device__ __forceinline__ int pick_radix(int rem) {
 // Forward FFT of nseq padded sequences of length n (2^a 3^b) held at x + s * ss; ping-pongs
 // between x and y and returns the buffer holding the result. Ends with a barrier. Not
 // inlined: one copy of the unrolled radix passes serves every call site (instruction
-// cache).
-__device__ __noinline__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, int ss,
-                            const float2 *__restrict__ tw, int tid, int nthr) {
+// cache). Powers of two take a copy with the radix-16/8/4/2 passes only, whose smaller
+// code stays resident in the instruction cache across the transform phases.
+template <bool POW2>
+__device__ __forceinline__ float2 *fft_smem_impl(float2 *x, float2 *y, int n, int nseq, int ss,
+                                                 const float2 *__restrict__ tw, int tid, int nthr) {
   float2 *in = x, *out = y;
   int Ns = 1, rem = n;
   while (rem > 1) {
     const int r = pick_radix(rem);
-    switch (r) {
-      case 16: stockham_pass<16>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      case 12: stockham_pass<12>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      case 8: stockham_pass<8>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      case 6: stockham_pass<6>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      case 4: stockham_pass<4>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      case 3: stockham_pass<3>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
-      default: stockham_pass<2>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+    if (POW2) {
+      switch (r) {
+        case 16: stockham_pass<16>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 8: stockham_pass<8>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 4: stockham_pass<4>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        default: stockham_pass<2>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      }
+    } else {
+      switch (r) {
+        case 16: stockham_pass<16>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 12: stockham_pass<12>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 8: stockham_pass<8>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 6: stockham_pass<6>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 4: stockham_pass<4>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        case 3: stockham_pass<3>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+        default: stockham_pass<2>(in, out, n, nseq, ss, Ns, tw, tid, nthr); break;
+      }
     }
     __syncthreads();
     float2 *tmp = in;
@@ -227,6 +238,22 @@ __device__ __noinline__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, 
     rem /= r;
   }
   return in;
+}
+
+__device__ __noinline__ float2 *fft_smem_pow2(float2 *x, float2 *y, int n, int nseq, int ss,
+                                              const float2 *__restrict__ tw, int tid, int nthr) {
+  return fft_smem_impl<true>(x, y, n, nseq, ss, tw, tid, nthr);
+}
+
+__device__ __noinline__ float2 *fft_smem_mixed(float2 *x, float2 *y, int n, int nseq, int ss,
+                                               const float2 *__restrict__ tw, int tid, int nthr) {
+  return fft_smem_impl<false>(x, y, n, nseq, ss, tw, tid, nthr);
+}
+
+__device__ __forceinline__ float2 *fft_smem(float2 *x, float2 *y, int n, int nseq, int ss,
+                                            const float2 *__restrict__ tw, int tid, int nthr) {
+  return (n & (n - 1)) == 0 ? fft_smem_pow2(x, y, n, nseq, ss, tw, tid, nthr)
+                            : fft_smem_mixed(x, y, n, nseq, ss, tw, tid, nthr);
 }
 
 // Copies `total` elements with U independent loads in flight per thread (load all, then

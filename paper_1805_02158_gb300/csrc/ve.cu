@@ -305,19 +305,40 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   constexpr int NP = K * (K + 1) / 2;
   constexpr int kap = K - 1;
   const int lane = threadIdx.x & 31;
+  // Sums of the chunk partials in double-float (FP32 TwoSum; the partials themselves carry
+  // the double-float accuracy of k_gram), fixed lane-strided order then a fixed xor tree:
+  // the FP64 units, a small fraction of the FP32 ones on this part, are kept for the
+  // factorisation.
   double G[K][K];
 #pragma unroll
   for (int i = 0, q = 0; i < K; ++i)
 #pragma unroll
     for (int j = i; j < K; ++j, ++q) {
-      double s = 0.0;
-      for (int c = lane; c < P->n_chunks; c += 32) s += P->gram_part[(size_t)c * kMaxPairs + q];
+      float h = 0.f, l = 0.f;
+      for (int c = lane; c < P->n_chunks; c += 32) {
+        const double v = P->gram_part[(size_t)c * kMaxPairs + q];
+        const float vh = __double2float_rn(v);
+        const float vl = __double2float_rn(v - (double)vh);
+        const float s = __fadd_rn(h, vh);
+        const float z = __fsub_rn(s, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(vh, z));
+        h = s;
+        l = __fadd_rn(l, __fadd_rn(e, vl));
+      }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      G[i][j] = s;
+      for (int off = 16; off > 0; off >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+        const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+        const float s = __fadd_rn(h, h2);
+        const float z = __fsub_rn(s, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
+        h = s;
+        l = __fadd_rn(__fadd_rn(l, l2), e);
+      }
+      G[i][j] = (double)h + (double)l;
     }
   (void)NP;
-  double R[K][K];
+  double R[K][K], inv[K];   // inv[j] = 1 / r_jj (one division per pivot)
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
@@ -338,12 +359,13 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
     }
     const double rjj = sqrt(s);
     R[j][j] = rjj;
+    inv[j] = 1.0 / rjj;
 #pragma unroll
     for (int l = j + 1; l < K; ++l) {
       double t = G[j][l];
 #pragma unroll
       for (int i = 0; i < j; ++i) t -= R[i][j] * R[i][l];
-      R[j][l] = t / rjj;
+      R[j][l] = t * inv[j];
     }
   }
   double gamma[K];
@@ -362,14 +384,15 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
         double s = -R[i][kap];
 #pragma unroll
         for (int j = i + 1; j < kap; ++j) s -= R[i][j] * c[j];
-        c[i] = s / R[i][i];
+        c[i] = s * inv[i];
       }
       double sc = 0.0, sa = 0.0;
 #pragma unroll
       for (int i = 0; i <= kap; ++i) { sc += c[i]; sa += fabs(c[i]); }
       if (fabs(sc) <= kSumTol * sa) ok = false;
+      const double isc = 1.0 / sc;
 #pragma unroll
-      for (int i = 0; i <= kap; ++i) gamma[i] = c[i] / sc;
+      for (int i = 0; i <= kap; ++i) gamma[i] = c[i] * isc;
     } else {
       // RRE: R^T z = 1 (forward), R d = z (backward), gamma = d / sum d
       double z[K], d[K];
@@ -378,20 +401,21 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
         double s = 1.0;
 #pragma unroll
         for (int j = 0; j < i; ++j) s -= R[j][i] * z[j];
-        z[i] = s / R[i][i];
+        z[i] = s * inv[i];
       }
 #pragma unroll
       for (int i = K - 1; i >= 0; --i) {
         double s = z[i];
 #pragma unroll
         for (int j = i + 1; j < K; ++j) s -= R[i][j] * d[j];
-        d[i] = s / R[i][i];
+        d[i] = s * inv[i];
       }
       double sd = 0.0;
 #pragma unroll
       for (int i = 0; i < K; ++i) sd += d[i];
+      const double isd = 1.0 / sd;
 #pragma unroll
-      for (int i = 0; i < K; ++i) gamma[i] = d[i] / sd;
+      for (int i = 0; i < K; ++i) gamma[i] = d[i] * isd;
     }
   }
   if (lane != 0) return;
