@@ -104,9 +104,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def problem_seeds(rank):
+    """Seeds of the images a rank solves: ranks take disjoint consecutive blocks (replicas
+    of the workload on distinct images, weak scaling)."""
+    return [rank * N_IMAGES + i for i in range(N_IMAGES)]
+
+
 def make_problems(rank):
     from paper_1805_02158_gb300 import synth
-    return [synth.deblur_gauss256(rank * N_IMAGES + i, SIDE) for i in range(N_IMAGES)]
+    return [synth.deblur_gauss256(s, SIDE) for s in problem_seeds(rank)]
+
+
+def max_over_ranks(dist, x):
+    """The maximum of a per-rank time over all ranks (the job's time); identity at N = 1."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_oracle_sample(seconds_target=12.0):
@@ -368,11 +385,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     launches = red.kernel_launches() - l0
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, float(sum(step_ms)))
 
     # per-kernel device times: the same K steps with CUDA events recorded around every
     # phase on the solve's stream (inside the cycle graph when the driver supports timing
@@ -416,11 +429,7 @@ def main():
             t0 = time.perf_counter()
             B.solve_host(y_h, x0_h, out_h, CALLS, 0.0)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_total = float(sum(e2e_ms))
-        if dist:
-            t = torch.tensor([e2e_total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+        e2e_total = max_over_ranks(dist, float(sum(e2e_ms)))
         h2d = sum(int(y.numel()) * 4 for y in y_h) + sum(int(x.numel()) * 4 for x in x0_h)
         d2h = sum(int(o.numel()) * 4 for o in out_h)
         e2e = {"value": units / (e2e_total / 1e3) / 1e6, "unit": UNIT,
