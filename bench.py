@@ -22,6 +22,7 @@ import argparse  # noqa: E402
 import json  # noqa: E402
 import math  # noqa: E402
 import subprocess  # noqa: E402
+import tempfile  # noqa: E402
 import sys  # noqa: E402
 import time  # noqa: E402
 
@@ -62,7 +63,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.path = os.path.join(os.environ.get("RED_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"red_bench_clocks_gpu{gpu_index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
