@@ -8,10 +8,12 @@
 //     W/2-point complex FFT is taken and the W/2 + 1 non-redundant bins are untangled;
 //   columns: forward FFT, the pointwise solve X = C + G F, inverse FFT;
 //   rows, complex-to-real, with the relative-change statistics of the FP step.
-// Two implementations with bitwise identical arithmetic:
+// Two implementations of the same transforms:
 //   * k_fft_solve_cluster: one thread-block cluster per problem, the half spectrum in the
-//     cluster's shared memory, transposed through distributed shared memory (images up
-//     to 512 x 512);
+//     cluster's shared memory; each CTA pushes its row band's bins into the column buffers
+//     of the CTAs owning the columns (remote stores through distributed shared memory),
+//     and after the column solve scatters them back the same way: two cluster barriers
+//     per FP step (images up to 384 x 384 with 16 CTAs);
 //   * k_fft_r2c / k_fft_cols / k_fft_c2r: three passes through global memory (any size).
 // Transforms are self-sorting Stockham passes in shared memory with register-resident
 // radix 16, 12, 8, 6, 4, 3 and 2 butterflies (sizes 2^a 3^b): few passes, so few
@@ -545,10 +547,11 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
 
 // The whole solve of one FP step for one problem in one thread-block cluster, with the
 // half spectrum held in the cluster's shared memory:
-//   rows R2C of the CTA's row band -> A (rows x (W/2+1), local shared memory)
-//   cluster barrier; each CTA gathers its band of spectrum columns from every CTA's A
-//   through distributed shared memory, column FFT, X = C + G F, inverse column FFT
-//   cluster barrier; each CTA scatters its columns back into the owners' A
+//   rows R2C of the CTA's row band; every bin is stored straight into the column buffer
+//   Rb of the CTA owning its column (distributed shared memory)
+//   cluster barrier; column FFT, X = C + G F, inverse column FFT; each CTA stores its
+//   columns back into the row-band buffer A of the rows' owners (A is touched by nobody
+//   before, so no barrier is needed first)
 //   cluster barrier; rows C2R of the band -> x_{k+1}, statistics; the last CTA to finish
 //   sums the per-CTA statistics and runs the termination test.
 // Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
@@ -579,9 +582,10 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   float2 *twm = sm;
   float2 *tww = twm + tw_cap_m;
   float2 *twh = tww + tw_cap_m + 1;
-  float2 *A = twh + tw_cap_h;
+  float2 *A = twh + tw_cap_h;       // row band of the solved half spectrum (phase 3 -> 4)
   float2 *X0 = A + a_cap;
   float2 *X1 = X0 + buf_cap;
+  float2 *Rb = X1 + buf_cap;        // this CTA's spectrum columns, pushed by every band
   const int tid = threadIdx.x, nthr = blockDim.x;
   const FastDiv fdm(M), fdwh(Wh), fdc(nc > 0 ? nc : 1);
   // x_k for the statistics, fetched first (its latency hides behind the transforms)
@@ -624,28 +628,20 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       });
   __syncthreads();
   const float2 *Z = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
+  // 2. push: every half-spectrum bin of the band's rows goes straight into the column
+  //    buffer of the CTA that owns its column (remote stores, no round trip), then one
+  //    cluster barrier makes the columns complete
+  const FastDiv by_wh(Wh);
   for (int idx = tid; idx < nr * Wh; idx += nthr) {
     int row, kk;
     fdwh.divmod(idx, row, kk);
-    A[row * Wh + kk] = r2c_bin(Z + row * ssm, M, kk, tww);
+    const float2 v = r2c_bin(Z + row * ssm, M, kk, tww);
+    const int q = band_owner(kk, ncta, by_wh);
+    float2 *Rq = cl.map_shared_rank(Rb, q);
+    Rq[(kk - band_lo(q, Wh, by_ncta)) * ssh + pidx(r0 + row)] = v;
   }
   cl.sync();
-  // 2. gather this CTA's spectrum columns from every row band
-  copy_batched<8>(H * nc, tid, nthr,
-      [&](int idx) {
-        int h, c;
-        fdc.divmod(idx, h, c);
-        const int q = band_owner(h, ncta, by_h);
-        const float2 *Aq = cl.map_shared_rank(A, q);
-        return Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c];
-      },
-      [&](int idx, float2 v) {
-        int h, c;
-        fdc.divmod(idx, h, c);
-        X0[c * ssh + pidx(h)] = v;
-      });
-  __syncthreads();
-  float2 *F = fft_smem(X0, X1, H, nc, ssh, twh, tid, nthr);
+  float2 *F = fft_smem(Rb, X0, H, nc, ssh, twh, tid, nthr);
   for (int base = tid; base < H * nc; base += 4 * nthr) {
     float2 cc[4];
     float gg[4];
@@ -672,9 +668,9 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     }
   }
   __syncthreads();
-  const float2 *Xs = fft_smem(F, F == X0 ? X1 : X0, H, nc, ssh, twh, tid, nthr);
-  cl.sync();   // every CTA has finished reading the A bands
-  // 3. scatter the solved columns back to the row bands
+  const float2 *Xs = fft_smem(F, F == Rb ? X0 : Rb, H, nc, ssh, twh, tid, nthr);
+  // 3. scatter the solved columns back to the row bands (A is read only by its own CTA,
+  //    after the next barrier, so no barrier is needed before the remote stores)
   for (int idx = tid; idx < H * nc; idx += nthr) {
     int h, c;
     fdc.divmod(idx, h, c);
@@ -849,7 +845,7 @@ void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems) {
 }
 
 int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
-  return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 2 * (size_t)buf_cap) * sizeof(float2));
+  return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 3 * (size_t)buf_cap) * sizeof(float2));
 }
 
 cudaError_t fft_cluster_prepare(int smem, int ncta) {
