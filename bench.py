@@ -394,7 +394,7 @@ def main():
     # graph-recorded events, else with the cycle launched directly)
     timing_mode = "direct launches (phase-timed pass)"
     B.set_phase_timing(True)
-    nlm_ms, fft_ms, gram_ms, comb_ms, pstep_ms = [], [], [], [], []
+    nlm_ms, fft_ms, gram_ms, comb_ms, vs_ms, pstep_ms = [], [], [], [], [], []
     B.solve(x0s, outs, CALLS, 0.0)
     for i in range(args.steps):
         flush.fill_(float(i))
@@ -409,6 +409,7 @@ def main():
         fft_ms.append(B.phase_ms(red.PHASE_FFT)[0])
         gram_ms.append(B.phase_ms(red.PHASE_GRAM)[0])
         comb_ms.append(B.phase_ms(red.PHASE_COMBINE)[0])
+        vs_ms.append(B.phase_ms(red.PHASE_VESOLVE)[0])
     B.set_phase_timing(False)
 
     pix = SIDE * SIDE * N_IMAGES
@@ -455,6 +456,8 @@ def main():
                  "GBps": gram_bytes / (np.mean(gram_ms) / 1e3) / 1e9},
         "combine": {"ms": float(np.mean(comb_ms)), "algorithmic_bytes": comb_bytes,
                     "GBps": comb_bytes / (np.mean(comb_ms) / 1e3) / 1e9},
+        "ve_solve": {"ms": float(np.mean(vs_ms))},
+        "nlm": {"ms": float(np.mean(nlm_ms))},
         "hbm_peak_GBps": hbm,
     }
     traffic = None
