@@ -306,38 +306,45 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   constexpr int kap = K - 1;
   const int lane = threadIdx.x & 31;
   // Sums of the chunk partials in double-float (FP32 TwoSum; the partials themselves carry
-  // the double-float accuracy of k_gram), fixed lane-strided order then a fixed xor tree:
-  // the FP64 units, a small fraction of the FP32 ones on this part, are kept for the
-  // factorisation.
+  // the double-float accuracy of k_gram): lane-strided over the chunks, all NP partials of
+  // a chunk loaded together, then a fixed xor tree. The FP64 units, a small fraction of the
+  // FP32 ones on this part, are kept for the factorisation.
+  float h[NP], l[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) h[q] = l[q] = 0.f;
+  for (int c = lane; c < P->n_chunks; c += 32) {
+    double v[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v[q] = __ldcg(P->gram_part + (size_t)c * kMaxPairs + q);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float vh = __double2float_rn(v[q]);
+      const float vl = __double2float_rn(v[q] - (double)vh);
+      const float s = __fadd_rn(h[q], vh);
+      const float z = __fsub_rn(s, h[q]);
+      const float e = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, z)), __fsub_rn(vh, z));
+      h[q] = s;
+      l[q] = __fadd_rn(l[q], __fadd_rn(e, vl));
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h[q], off);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l[q], off);
+      const float s = __fadd_rn(h[q], h2);
+      const float z = __fsub_rn(s, h[q]);
+      const float e = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, z)), __fsub_rn(h2, z));
+      h[q] = s;
+      l[q] = __fadd_rn(__fadd_rn(l[q], l2), e);
+    }
+  }
   double G[K][K];
 #pragma unroll
   for (int i = 0, q = 0; i < K; ++i)
 #pragma unroll
-    for (int j = i; j < K; ++j, ++q) {
-      float h = 0.f, l = 0.f;
-      for (int c = lane; c < P->n_chunks; c += 32) {
-        const double v = P->gram_part[(size_t)c * kMaxPairs + q];
-        const float vh = __double2float_rn(v);
-        const float vl = __double2float_rn(v - (double)vh);
-        const float s = __fadd_rn(h, vh);
-        const float z = __fsub_rn(s, h);
-        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(vh, z));
-        h = s;
-        l = __fadd_rn(l, __fadd_rn(e, vl));
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
-        const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
-        const float s = __fadd_rn(h, h2);
-        const float z = __fsub_rn(s, h);
-        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
-        h = s;
-        l = __fadd_rn(__fadd_rn(l, l2), e);
-      }
-      G[i][j] = (double)h + (double)l;
-    }
-  (void)NP;
+    for (int j = i; j < K; ++j, ++q) G[i][j] = (double)h[q] + (double)l[q];
   double R[K][K], inv[K];   // inv[j] = 1 / r_jj (one division per pivot)
 #pragma unroll
   for (int i = 0; i < K; ++i)
