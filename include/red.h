@@ -223,9 +223,11 @@ red_status red_batch_describe(red_batch b, char *buf, size_t len);
 /* Serving: a request loop that continuously batches RED solves of different sizes and  */
 /* tasks as they arrive. Requests are admitted while their device footprint fits in     */
 /* hbm_budget_bytes and a slot is free; each running request keeps its iterate history  */
-/* and constants on the device; every scheduler tick advances all running requests by   */
-/* one FP step (batched launches) and retires finished ones, freeing room for waiting    */
-/* requests. All server functions are thread-safe.                                      */
+/* and constants on the device. Requests of one task, size class and extrapolation     */
+/* setting share launches and advance one Algorithm 3 cycle at a time on their own      */
+/* stream; finished requests are retired after each cycle, freeing room for waiting     */
+/* ones. A request's result does not depend on the others in flight. All server         */
+/* functions are thread-safe.                                                           */
 /* ----------------------------------------------------------------------------------- */
 
 red_status red_server_create(size_t hbm_budget_bytes, int max_slots, red_server *out);

@@ -713,7 +713,7 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
       out.put((long)(r0 + row) * W + 2 * n, v.x, -v.y, pv[u], sd, sx);
     }
   }
-  // CTA sums (fixed order), then rank 0 sums the cluster's partials in rank order
+  // CTA sums (fixed order); the per-CTA partials are summed below by the last CTA to arrive
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
