@@ -169,9 +169,13 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+STUDY_VARIANTS = (("rre", 5), ("mpe", 5), ("rre", 10), ("mpe", 10))
+
+
 def ve_vs_fp_study(problems, Ps, torch, red):
-    """Denoiser calls RRE needs to reach plain FP's PSNR and objective after 200 calls
-    (the Table I criterion), per image; outside the timed region."""
+    """Denoiser calls each extrapolation variant (RRE/MPE, k = 5/10) needs to reach plain
+    FP's objective and PSNR after 200 calls (the Table I criterion), per image, probing
+    budgets in steps of 5 calls; outside the timed region. None: not reached within 200."""
     from paper_1805_02158_gb300.red import Batch
     n = len(problems)
     x0s = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
@@ -183,25 +187,37 @@ def ve_vs_fp_study(problems, Ps, torch, red):
     xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
     psnr_fp = [10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2)) for x, p in zip(xfp, problems)]
     e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
-    Bv = Batch(Ps)
-    need_psnr = [None] * n
-    need_cost = [None] * n
-    for calls in range(5, CALLS + 1, 5):
-        Bv.solve(x0s, outs, calls, 0.0)
-        for i, (o, p, P) in enumerate(zip(outs, problems, Ps)):
-            x = o.cpu().numpy().astype(np.float64)
-            ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
-            if need_psnr[i] is None and ps >= psnr_fp[i]:
-                need_psnr[i] = calls
-            if need_cost[i] is None and P.objective(o) <= e_fp[i]:
-                need_cost[i] = calls
-        if all(v is not None for v in need_psnr + need_cost):
-            break
-    fill = lambda v: [c if c is not None else CALLS for c in v]  # noqa: E731
+    del B, fpP
+    variants = {}
+    for method, k in STUDY_VARIANTS:
+        VP = Ps if (method, k) == ("rre", VE_K) else \
+            [red.Problem(red.config_for(p, ve=method, ve_k=k), x) for p, x in zip(problems, x0s)]
+        Bv = Batch(VP)
+        need_psnr = [None] * n
+        need_cost = [None] * n
+        for calls in range(5, CALLS + 1, 5):
+            Bv.solve(x0s, outs, calls, 0.0)
+            for i, (o, p, P) in enumerate(zip(outs, problems, VP)):
+                x = o.cpu().numpy().astype(np.float64)
+                ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
+                if need_psnr[i] is None and ps >= psnr_fp[i]:
+                    need_psnr[i] = calls
+                if need_cost[i] is None and P.objective(o) <= e_fp[i]:
+                    need_cost[i] = calls
+            if all(v is not None for v in need_psnr + need_cost):
+                break
+        reached = lambda v: [c for c in v if c is not None]  # noqa: E731
+        variants[f"{method}_k{k}"] = {
+            "calls_to_fp200_cost": need_cost, "calls_to_fp200_psnr": need_psnr,
+            "cost_reached": len(reached(need_cost)), "psnr_reached": len(reached(need_psnr)),
+            "cost_calls_mean_reached": float(np.mean(reached(need_cost))) if reached(need_cost) else None,
+            "psnr_calls_mean_reached": float(np.mean(reached(need_psnr))) if reached(need_psnr) else None}
+        del Bv
+    main = variants[f"rre_k{VE_K}"]
     return {"fp_calls": CALLS, "fp200_psnr_db_mean": float(np.mean(psnr_fp)),
-            "rre_calls_to_fp200_psnr": fill(need_psnr), "rre_calls_to_fp200_cost": fill(need_cost),
-            "rre_calls_to_fp200_psnr_mean": float(np.mean(fill(need_psnr))),
-            "rre_calls_to_fp200_cost_mean": float(np.mean(fill(need_cost)))}
+            "rre_calls_to_fp200_cost_mean": main["cost_calls_mean_reached"],
+            "rre_calls_to_fp200_psnr_mean": main["psnr_calls_mean_reached"],
+            "variants": variants}
 
 
 def secondary_workloads(red, torch, flush, steps=3, warmup=3):
