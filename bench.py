@@ -172,16 +172,18 @@ def run_reference(args, rank, world):
 STUDY_VARIANTS = (("rre", 5), ("mpe", 5), ("rre", 10), ("mpe", 10))
 
 
-def ve_vs_fp_study(problems, Ps, torch, red):
+def ve_vs_fp_study(problems, Ps, torch, red, variants_to_run=STUDY_VARIANTS):
     """Denoiser calls each extrapolation variant (RRE/MPE, k = 5/10) needs to reach plain
-    FP's objective and PSNR after 200 calls (the Table I criterion), per image, probing
-    budgets in steps of 5 calls; outside the timed region. None: not reached within 200."""
+    FP's objective and PSNR after 200 calls (the criterion of Tables I and II), per image,
+    probing budgets in steps of 5 calls; outside the timed region. None: not reached
+    within 200. Ps: problems already configured for RRE with k = 5 (reused), or None."""
     from paper_1805_02158_gb300.red import Batch
     n = len(problems)
-    x0s = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
+    ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
+    x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in problems]
     outs = [torch.empty_like(x) for x in x0s]
     fp_cfgs = [red.config_for(p, ve="none") for p in problems]
-    fpP = [red.Problem(c, x) for c, x in zip(fp_cfgs, x0s)]
+    fpP = [red.Problem(c, y) for c, y in zip(fp_cfgs, ys)]
     B = Batch(fpP)
     B.solve(x0s, outs, CALLS, 0.0)
     xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
@@ -189,9 +191,9 @@ def ve_vs_fp_study(problems, Ps, torch, red):
     e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
     del B, fpP
     variants = {}
-    for method, k in STUDY_VARIANTS:
-        VP = Ps if (method, k) == ("rre", VE_K) else \
-            [red.Problem(red.config_for(p, ve=method, ve_k=k), x) for p, x in zip(problems, x0s)]
+    for method, k in variants_to_run:
+        VP = Ps if (Ps is not None and (method, k) == ("rre", VE_K)) else \
+            [red.Problem(red.config_for(p, ve=method, ve_k=k), y) for p, y in zip(problems, ys)]
         Bv = Batch(VP)
         need_psnr = [None] * n
         need_cost = [None] * n
@@ -213,10 +215,10 @@ def ve_vs_fp_study(problems, Ps, torch, red):
             "cost_calls_mean_reached": float(np.mean(reached(need_cost))) if reached(need_cost) else None,
             "psnr_calls_mean_reached": float(np.mean(reached(need_psnr))) if reached(need_psnr) else None}
         del Bv
-    main = variants[f"rre_k{VE_K}"]
+    main = variants.get(f"rre_k{VE_K}", {})
     return {"fp_calls": CALLS, "fp200_psnr_db_mean": float(np.mean(psnr_fp)),
-            "rre_calls_to_fp200_cost_mean": main["cost_calls_mean_reached"],
-            "rre_calls_to_fp200_psnr_mean": main["psnr_calls_mean_reached"],
+            "rre_calls_to_fp200_cost_mean": main.get("cost_calls_mean_reached"),
+            "rre_calls_to_fp200_psnr_mean": main.get("psnr_calls_mean_reached"),
             "variants": variants}
 
 
@@ -484,9 +486,12 @@ def main():
         except Exception:
             traffic = None
 
-    study = None
+    study = study_sr = None
     if not args.no_study and rank == 0:
         study = ve_vs_fp_study(problems, Ps, torch, red)
+        from paper_1805_02158_gb300 import synth as _synth
+        study_sr = ve_vs_fp_study([_synth.sr_x3(i) for i in range(9)], None, torch, red,
+                                  (("mpe", 5), ("rre", 5)))
     secondary = None
     if not args.no_secondary and rank == 0:
         secondary = secondary_workloads(red, torch, flush)
@@ -520,6 +525,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
         "ve_vs_fp": study,
+        "ve_vs_fp_sr": study_sr,
         "other_workloads": secondary,
         "serving": serving,
     }
