@@ -74,7 +74,7 @@ typedef struct {
   double nlm_h;          /* NLM filtering parameter h (weights exp(-d/h^2), d the mean  */
                          /* squared patch difference)                                    */
   int ve;                /* red_ve                                                      */
-  int ve_k;              /* FP steps per cycle = columns of U = kappa + 1 (1..16)        */
+  int ve_k;              /* FP steps per cycle = columns of U = kappa + 1 (1..12)        */
   int ve_m;              /* lead-in FP steps per cycle before the stored window (>= 0)   */
   int cg_iters;          /* CG iterations per FP step for SR (e.g. 20)                   */
   int storage;           /* red_dtype of the iterate history (F32 or BF16)               */
@@ -124,7 +124,7 @@ red_status red_denoise(red_problem p, const void *x_dev, void *f_dev, void *stre
 
 /* One extrapolation (Algorithm 1 with the problem's ve method: MPE, RRE Eq. (19) or SVD-MPE) from
  * n_vec = kappa + 2 device float32 iterates xs_dev[0..n_vec) (x_m .. x_{m+kappa+1}), host
- * array of device pointers, 3 <= n_vec <= 17. Writes x_(m,kappa) to x_out_dev (may alias
+ * array of device pointers, 3 <= n_vec <= 13. Writes x_(m,kappa) to x_out_dev (may alias
  * xs_dev[0]). If gamma_host is non-null the call synchronises the stream and copies the
  * kappa + 1 weights gamma_i (double) there. Returns RED_EVE_BREAKDOWN (x_out = the last
  * iterate) when the extrapolation does not exist. */
@@ -138,9 +138,9 @@ red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_ve
  * process whose device memory is reserved up front by another allocator has no room for
  * a problem's buffers. No problem handle is needed and nothing is allocated: the Gram
  * partial sums, xi, gamma and the status live in one file-scope device array of
- * 1 MiB + 384 bytes per device (1024 rows of 136 partial sums, enough for any n).
+ * 624 KiB + 320 bytes per device (1024 rows of 78 partial sums, enough for any n).
  *   xs_dev:  host array of n_vec device pointers to float32 vectors x_m .. x_{m+kappa+1},
- *            each of n elements, 3 <= n_vec <= 17 (any alignment; 16-byte aligned
+ *            each of n elements, 3 <= n_vec <= 13 (any alignment; 16-byte aligned
  *            vectors take the vectorised path).
  *   n:       elements per vector, 1 <= n <= 2^31 - 1; larger n returns RED_EINVAL.
  *   method:  RED_VE_MPE (Algorithm 1), RED_VE_RRE (Eq. (19)) or RED_VE_SVDMPE.

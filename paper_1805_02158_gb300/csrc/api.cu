@@ -126,7 +126,7 @@ static void validate(const red_config *c) {
   if (c->task == RED_SR) CHECK_ARG(c->scale >= 2 && c->height / c->scale >= 1 && c->width / c->scale >= 1,
                                    "super-resolution needs scale >= 2");
   CHECK_ARG(c->ve >= RED_VE_NONE && c->ve <= RED_VE_SVDMPE, "bad ve method");
-  CHECK_ARG(c->ve_k >= 1 && c->ve_k <= kMaxK, "ve_k must be in [1, 16]");
+  CHECK_ARG(c->ve_k >= 1 && c->ve_k <= kMaxK, "ve_k must be in [1, 12]");
   CHECK_ARG(c->ve_m >= 0 && c->ve_m <= 64, "ve_m must be in [0, 64]");
   CHECK_ARG(c->cg_iters >= 0 && c->cg_iters <= 1000, "cg_iters must be in [0, 1000]");
   if (c->nlm_patch != 5 || c->nlm_search != 11)
@@ -596,7 +596,7 @@ red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_ve
                               void *x_out_dev, double *gamma_host, void *stream) {
   return guarded([&] {
     CHECK_ARG(p && xs_dev && x_out_dev, "null argument");
-    CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 17]");
+    CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 13]");
     CHECK_ARG(p->cfg.ve == RED_VE_MPE || p->cfg.ve == RED_VE_RRE || p->cfg.ve == RED_VE_SVDMPE,
               "the problem's ve method must be MPE, RRE or SVD-MPE");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -9,7 +9,7 @@
 
 namespace red {
 
-constexpr int kMaxK = 16;                       // largest ve_k (columns of U)
+constexpr int kMaxK = 12;                       // largest ve_k (columns of U)
 constexpr int kMaxPairs = kMaxK * (kMaxK + 1) / 2;
 constexpr int kGramChunk = 2048;                // pixels per Gram / combine work unit
 constexpr int kNlmR = 6;                        // output rows per NLM thread

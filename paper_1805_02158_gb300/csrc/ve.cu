@@ -247,11 +247,13 @@ __device__ bool svd_mpe_gamma(const double (&R)[K][K], double (&gamma)[K]) {
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     return x;
   };
+  // (the pair loops are rolled: SVD-MPE is not on the timed path, and unrolling them for
+  // every K would dominate the library's build time)
   for (int sweep = 0; sweep < 40; ++sweep) {
     bool rotated = false;
-#pragma unroll
+#pragma unroll 1
     for (int p = 0; p < K - 1; ++p) {
-#pragma unroll
+#pragma unroll 1
       for (int q = p + 1; q < K; ++q) {
         const double al = wsum(a[p] * a[p]), be = wsum(a[q] * a[q]), ga = wsum(a[p] * a[q]);
         if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
@@ -591,7 +593,7 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
 }
 
 #define RED_K_CASES(M) \
-  M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+  M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
 
 cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int update_state,
                             cudaStream_t s) {
@@ -640,7 +642,7 @@ constexpr int kStaticStateDoubles = 16;
 constexpr int kStaticDoubles = kStaticPartials + 2 * kMaxK + kStaticStateDoubles;
 static_assert(sizeof(ProbState) <= kStaticStateDoubles * sizeof(double), "state block");
 
-// 1,114,112 + 384 bytes: per-CTA Gram partials | xi | gamma | ProbState
+// 638,976 + 320 bytes: per-CTA Gram partials | xi | gamma | ProbState
 static __device__ __align__(256) double g_ve_scratch[kStaticDoubles];
 
 struct StaticVe {
@@ -821,7 +823,7 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
                                                 void *stream) {
   return guarded([&] {
     CHECK_ARG(xs_dev && x_out_dev, "null argument");
-    CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 17]");
+    CHECK_ARG(n_vec >= 3 && n_vec <= kMaxK + 1, "n_vec must be in [3, 13]");
     CHECK_ARG(method == RED_VE_MPE || method == RED_VE_RRE || method == RED_VE_SVDMPE,
               "method must be RED_VE_MPE, RED_VE_RRE or RED_VE_SVDMPE");
     CHECK_ARG(n >= 1, "n must be positive");
@@ -860,7 +862,7 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
     break;
       RED_K_CASES(RED_STATIC_CASE)
 #undef RED_STATIC_CASE
-      default: throw Fail{RED_EINVAL, "n_vec must be in [3, 17]"};
+      default: throw Fail{RED_EINVAL, "n_vec must be in [3, 13]"};
     }
     count_launches(3);
     CUDA_OK(cudaGetLastError());

@@ -59,7 +59,7 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(height=64, width=27), red.RED_EINVAL),           # odd width
     (dict(height=4, width=64), red.RED_EINVAL),            # too small
     (dict(sigma=0.0), red.RED_EINVAL),
-    (dict(ve_k=17), red.RED_EINVAL),
+    (dict(ve_k=13), red.RED_EINVAL),
     (dict(task="sr", scale=1), red.RED_EINVAL),
     (dict(ve=7), red.RED_EINVAL),                          # no such method
     (dict(storage="f16"), red.RED_EUNSUPPORTED),

@@ -128,8 +128,8 @@ def test_static_rejects_sizes_beyond_limit():
     st = L.red_ve_extrapolate_static(arr, 3, 2 ** 31, 2, ctypes.c_void_p(v.data_ptr()), gam, None)
     assert st == red.RED_EINVAL
     assert b"exceeds the limit" in L.red_last_error()
-    arr18 = (ctypes.c_void_p * 18)(*[v.data_ptr()] * 18)
-    st = L.red_ve_extrapolate_static(arr18, 18, 16, 2, ctypes.c_void_p(v.data_ptr()), gam, None)
+    arr14 = (ctypes.c_void_p * 14)(*[v.data_ptr()] * 14)
+    st = L.red_ve_extrapolate_static(arr14, 14, 16, 2, ctypes.c_void_p(v.data_ptr()), gam, None)
     assert st == red.RED_EINVAL
     st = L.red_ve_extrapolate_static(arr, 3, 16, 0, ctypes.c_void_p(v.data_ptr()), gam, None)
     assert st == red.RED_EINVAL
