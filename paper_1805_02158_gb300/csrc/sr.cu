@@ -133,7 +133,7 @@ template <int KH, int KW, int S, class RowP>
 __device__ void band_sb(const SrBand &g, RowP &&rowp, float beta, bool accumulate) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SrDims<KH, KW, S> d(g);
-  const int W = g.W, c1 = g.c1, c2 = g.c2;
+  const int W = g.W, c2 = g.c2;
   constexpr int kRowsMax = KH > 0 ? KH : 1;
   for (int k = warp; k < g.nz; k += kSrWarps) {
     const int li = g.lrow[k];
