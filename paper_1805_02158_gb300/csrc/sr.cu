@@ -15,7 +15,8 @@
 // So one CG iteration is
 //     A p (band, from shared z)  ->  p.Ap      [cluster barrier 1]
 //     x += a p, r -= a Ap (band)  ->  r.r      [cluster barrier 2]
-//     p = r + beta p (band);  z = S B r + beta z (band + halo rows of r)
+//     z = S B r + beta z (band + halo rows of r); p = r + beta p is folded into the next
+//     adjoint pass
 // with two barriers. The adjoint pass for the 7x7 / x3 workload gives each lane s
 // consecutive columns, which together use every tap of a sampled row once (other extents:
 // lanes take columns of one residue mod s). Dot products: each warp's partial goes to
@@ -517,11 +518,13 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   band_sb<KH, KW, S>(g, r_row, 0.f, false);   // z = S B p, p = r
   __syncthreads();
 
+  float beta = 0.f;   // p = r + beta p is applied in the adjoint pass (p = r at first)
   for (int it = 0; it < P->cg_iters; ++it) {
     if (rr == 0.f) break;
     dot = 0.f;
     band_adjoint<KH, KW, S>(g, [&](long e, int l, float acc) {
-      const float pv = ps[l];
+      const float pv = fmaf(beta, ps[l], rs[l]);
+      ps[l] = pv;
       const float apv = fmaf(acc, is2, alpha * pv);
       aps[l] = apv;
       dot = fmaf(pv, apv, dot);
@@ -554,24 +557,8 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       }
     }
     const float rr_new = cluster_total(cl, slot_b, dot, ncta);
-    const float beta = rr_new / rr;
+    beta = rr_new / rr;
     rr = rr_new;
-    for (int l0 = tid; l0 < nl; l0 += kU * kSrThreads) {
-      float pv[kU], rv[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int l = l0 + u * kSrThreads;
-        if (l < nl) {
-          pv[u] = ps[l];
-          rv[u] = rs[l];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int l = l0 + u * kSrThreads;
-        if (l < nl) ps[l] = fmaf(beta, pv[u], rv[u]);
-      }
-    }
     if (resident) {
       fill_halo(rh, rs);
       __syncthreads();
