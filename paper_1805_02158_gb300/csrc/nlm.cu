@@ -31,6 +31,7 @@ namespace {
 constexpr int kCols = kNlmTW + 14;   // staged columns: [tc0 - 7, tc0 + 67)
 constexpr int kStride = 76;          // shared-memory row stride (floats)
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStageU = 48;          // tile loads in flight per lane (the whole tile at once)
 
 // Half-sample symmetric reflection for indices within one side length of the image,
 // then clamped into it.
@@ -75,15 +76,15 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
           (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
   }
 
-  // Stage the tile: 8 loads in flight per lane. One reflection is exact for every pixel
-  // an output inside the image needs (halo 7 <= side); the clamp only keeps rows/columns
-  // of partial tiles, whose outputs are not stored, inside the image.
+  // Stage the tile: kStageU loads in flight per lane. One reflection is exact for every
+  // pixel an output inside the image needs (halo 7 <= side); the clamp only keeps
+  // rows/columns of partial tiles, whose outputs are not stored, inside the image.
   const int tid = threadIdx.x;
   const int total = rows * kCols;
-  for (int base = tid; base < total; base += 8 * 32) {
-    float v[8];
+  for (int base = tid; base < total; base += kStageU * 32) {
+    float v[kStageU];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStageU; ++u) {
       const int idx = base + u * 32;
       if (idx < total) {
         const int rr = idx / kCols;
@@ -94,7 +95,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStageU; ++u) {
       const int idx = base + u * 32;
       if (idx < total) {
         const int rr = idx / kCols;
