@@ -463,6 +463,16 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     pk, pk_src = peaks()
+    measured_units = None
+    if rank == 0:
+        try:
+            mu = red.measure_peaks()
+            measured_units = {"fp32_fma_T_lane_ops": mu["fp32_fma"] / 1e12,
+                              "ex2_T_lane_ops": mu["ex2"] / 1e12,
+                              "fp64_fma_T_lane_ops": mu["fp64_fma"] / 1e12,
+                              "how": "independent FMA / ex2.approx chains on every SM (red_measure_peaks)"}
+        except Exception as e:  # noqa: BLE001
+            measured_units = {"error": str(e)}
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     nlm_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12          # FP32 lane-ops, T/s
@@ -532,6 +542,7 @@ def main():
                      "frac": nlm_achieved / nlm_peak, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_src} max clock)",
                      "launch_ms": nlm_avg, "timing": f"CUDA events around each launch, {timing_mode}",
+                     "measured_units": measured_units,
                      "step_ms_with_phase_events": float(np.mean(pstep_ms))},
         "kernels": kern,
         "cpu_baseline": cpu,

@@ -259,6 +259,14 @@ const char *red_last_error(void);
 /* Bytes of device memory a problem with this config allocates (admission accounting). */
 red_status red_problem_footprint(const red_config *cfg, size_t *bytes);
 
+/* Measures the throughput of the arithmetic units the hot path is bound by, in lane
+ * operations per second over the whole device: FP32 FMA (the NLM's arithmetic), the
+ * ex2.approx special function (its weights) and FP64 FMA (the extrapolation solve), each by
+ * independent dependency chains on every SM (a few ms; synchronises the stream). No
+ * counterpart in the paper: it puts measured peaks beside the derived ones of the roofline. */
+red_status red_measure_peaks(double *fp32_fma_lane_ops, double *ex2_lane_ops,
+                             double *fp64_fma_lane_ops, void *stream);
+
 /* Number of kernel launches this library has issued in this process (for accounting). */
 uint64_t red_kernel_launches(void);
 

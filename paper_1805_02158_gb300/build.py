@@ -21,7 +21,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libred.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["nlm.cu", "fft.cu", "ve.cu", "sr.cu", "api.cu", "batch.cu", "server.cpp"]
+SOURCES = ["nlm.cu", "fft.cu", "ve.cu", "sr.cu", "api.cu", "batch.cu", "server.cpp", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -103,6 +103,8 @@ _SIGS = {
     "red_last_error": (ctypes.c_char_p, []),
     "red_problem_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
     "red_kernel_launches": (ctypes.c_uint64, []),
+    "red_measure_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
 }
 
 
@@ -120,6 +122,14 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def measure_peaks(stream=None):
+    """Measured FP32-FMA, EX2 and FP64-FMA throughputs (lane operations / s, whole device)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().red_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                   _stream_ptr(stream)), "red_measure_peaks")
+    return {"fp32_fma": a.value, "ex2": b.value, "fp64_fma": c.value}
 
 
 def status_string(st: int) -> str:

@@ -256,3 +256,13 @@ def test_extrapolation_breakdown_reported():
     st, gamma = P.ve_extrapolate(xs, out)
     assert st == red.RED_EVE_BREAKDOWN and gamma is None
     assert float((out - xs[-1]).abs().max()) == 0.0
+
+
+def test_measured_unit_peaks_are_plausible():
+    """The arithmetic-unit microbenchmarks: FP32 FMA near 152 SMs x 128 lanes x clock, the
+    special-function unit a fraction of it, FP64 far below FP32 on this part."""
+    torch_cuda()
+    m = red.measure_peaks()
+    assert 5e12 < m["fp32_fma"] < 60e12
+    assert 0 < m["ex2"] < m["fp32_fma"]
+    assert 0 < m["fp64_fma"] < m["fp32_fma"]
