@@ -224,6 +224,10 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   // the x0 host vector must outlive the copy
   CUDA_OK(cudaStreamSynchronize(s));
   r->t_admit = Clock::now();
+  // the observation now lives on the device: a finished request keeps only its status and
+  // statistics on the host
+  std::vector<float>().swap(r->y);
+  std::vector<float>().swap(r->psf);
 }
 
 // Launches one cycle of Algorithm 3 for the group's running requests on the group's
