@@ -371,7 +371,13 @@ def main():
         dist.init_process_group("nccl")
 
     import __graft_entry__
-    __graft_entry__.build()
+    # one rank per node compiles (the objects are shared), the others then load the library
+    if local == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    if local != 0:
+        __graft_entry__.build()   # up to date: nothing is recompiled
     from paper_1805_02158_gb300 import red
 
     problems = make_problems(rank)
