@@ -79,3 +79,30 @@ def test_ve_reaches_fp_objective_in_fewer_calls():
                 reached.append(c)
         red.solve(F, p.x0, method, m=0, kappa=4, max_calls=budget, callback=cb)
         assert reached and reached[0] < 0.75 * budget, (method, reached)
+
+
+@pytest.mark.parametrize("make", [small_deblur, small_sr])
+def test_objective_gradient_and_value_with_a_linear_denoiser(make):
+    """Eq. (4) against Eq. (5) where the RED prior is a plain quadratic: with a symmetric
+    linear denoiser f(x) = W x, rho(x) = x^T (x - W x) / 2 has gradient x - W x, so the
+    objective's central differences must equal the gradient of Eq. (5); E(0) = |y|^2/(2 s^2).
+    A dropped 1/2, sigma^2, alpha or transpose in either function fails this."""
+    p = make()
+    shape = (p.height, p.width)
+    otf = ops.psf_otf(p.psf, shape)
+    rng = np.random.default_rng(3)
+    n = p.height * p.width
+    A = rng.uniform(0, 1, (n, n))
+    Wm = (A + A.T) / (2 * n)                       # symmetric, spectral radius < 1
+    f = lambda v: (Wm @ v.ravel()).reshape(shape)  # noqa: E731
+    x = rng.uniform(0, 255, shape)
+    e = lambda v: red.objective(v, f(v), p.y, otf, p.scale, p.sigma, p.alpha)  # noqa: E731
+    g = red.gradient(x, f(x), p.y, otf, p.scale, p.sigma, p.alpha)
+    h = 1e-3
+    for idx in [(0, 0), (3, 5), (p.height - 1, p.width - 2), (7, 11)]:
+        d = np.zeros(shape)
+        d[idx] = h
+        num = (e(x + d) - e(x - d)) / (2 * h)
+        assert abs(num - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
+    assert e(np.zeros(shape)) == pytest.approx(float(np.vdot(p.y, p.y)) / (2 * p.sigma ** 2),
+                                               rel=1e-12)
