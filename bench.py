@@ -172,54 +172,114 @@ def run_reference(args, rank, world):
 STUDY_VARIANTS = (("rre", 5), ("mpe", 5), ("rre", 10), ("mpe", 10))
 
 
+def _fp_reference(problems, ys, x0s, outs, red):
+    """Plain FP (no extrapolation) after CALLS denoiser calls: per-image PSNR and objective."""
+    fpP = [red.Problem(red.config_for(p, ve="none"), y) for p, y in zip(problems, ys)]
+    B = red.Batch(fpP)
+    B.solve(x0s, outs, CALLS, 0.0)
+    xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
+    psnr_fp = [10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2)) for x, p in zip(xfp, problems)]
+    e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
+    return psnr_fp, e_fp
+
+
+def _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp, final_objective=False):
+    """Denoiser calls the solves of VP need to reach plain FP's PSNR and objective, probing
+    budgets in steps of 5 calls up to CALLS (None: not reached); optionally the objective
+    after CALLS calls as a fraction of plain FP's."""
+    n = len(problems)
+    Bv = red.Batch(VP)
+    need_psnr = [None] * n
+    need_cost = [None] * n
+    for calls in range(5, CALLS + 1, 5):
+        Bv.solve(x0s, outs, calls, 0.0)
+        for i, (o, p, P) in enumerate(zip(outs, problems, VP)):
+            x = o.cpu().numpy().astype(np.float64)
+            ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
+            if need_psnr[i] is None and ps >= psnr_fp[i]:
+                need_psnr[i] = calls
+            if need_cost[i] is None and P.objective(o) <= e_fp[i]:
+                need_cost[i] = calls
+        if all(v is not None for v in need_psnr + need_cost):
+            break
+    ratio = None
+    if final_objective:
+        Bv.solve(x0s, outs, CALLS, 0.0)
+        ratio = [P.objective(o) / e for P, o, e in zip(VP, outs, e_fp)]
+    return need_cost, need_psnr, ratio
+
+
+def _mean_reached(v):
+    r = [c for c in v if c is not None]
+    return float(np.mean(r)) if r else None
+
+
 def ve_vs_fp_study(problems, Ps, torch, red, variants_to_run=STUDY_VARIANTS):
     """Denoiser calls each extrapolation variant (RRE/MPE, k = 5/10) needs to reach plain
     FP's objective and PSNR after 200 calls (the criterion of Tables I and II), per image,
     probing budgets in steps of 5 calls; outside the timed region. None: not reached
     within 200. Ps: problems already configured for RRE with k = 5 (reused), or None."""
-    from paper_1805_02158_gb300.red import Batch
-    n = len(problems)
     ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
     x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in problems]
     outs = [torch.empty_like(x) for x in x0s]
-    fp_cfgs = [red.config_for(p, ve="none") for p in problems]
-    fpP = [red.Problem(c, y) for c, y in zip(fp_cfgs, ys)]
-    B = Batch(fpP)
-    B.solve(x0s, outs, CALLS, 0.0)
-    xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
-    psnr_fp = [10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2)) for x, p in zip(xfp, problems)]
-    e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
-    del B, fpP
+    psnr_fp, e_fp = _fp_reference(problems, ys, x0s, outs, red)
     variants = {}
     for method, k in variants_to_run:
         VP = Ps if (Ps is not None and (method, k) == ("rre", VE_K)) else \
             [red.Problem(red.config_for(p, ve=method, ve_k=k), y) for p, y in zip(problems, ys)]
-        Bv = Batch(VP)
-        need_psnr = [None] * n
-        need_cost = [None] * n
-        for calls in range(5, CALLS + 1, 5):
-            Bv.solve(x0s, outs, calls, 0.0)
-            for i, (o, p, P) in enumerate(zip(outs, problems, VP)):
-                x = o.cpu().numpy().astype(np.float64)
-                ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
-                if need_psnr[i] is None and ps >= psnr_fp[i]:
-                    need_psnr[i] = calls
-                if need_cost[i] is None and P.objective(o) <= e_fp[i]:
-                    need_cost[i] = calls
-            if all(v is not None for v in need_psnr + need_cost):
-                break
-        reached = lambda v: [c for c in v if c is not None]  # noqa: E731
+        need_cost, need_psnr, _ = _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp)
         variants[f"{method}_k{k}"] = {
             "calls_to_fp200_cost": need_cost, "calls_to_fp200_psnr": need_psnr,
-            "cost_reached": len(reached(need_cost)), "psnr_reached": len(reached(need_psnr)),
-            "cost_calls_mean_reached": float(np.mean(reached(need_cost))) if reached(need_cost) else None,
-            "psnr_calls_mean_reached": float(np.mean(reached(need_psnr))) if reached(need_psnr) else None}
-        del Bv
+            "cost_reached": sum(c is not None for c in need_cost),
+            "psnr_reached": sum(c is not None for c in need_psnr),
+            "cost_calls_mean_reached": _mean_reached(need_cost),
+            "psnr_calls_mean_reached": _mean_reached(need_psnr)}
     main = variants.get(f"rre_k{VE_K}", {})
     return {"fp_calls": CALLS, "fp200_psnr_db_mean": float(np.mean(psnr_fp)),
             "rre_calls_to_fp200_cost_mean": main.get("cost_calls_mean_reached"),
             "rre_calls_to_fp200_psnr_mean": main.get("psnr_calls_mean_reached"),
             "variants": variants}
+
+
+SWEEP_M = (0, 5, 10)
+SWEEP_KAPPA = (3, 5, 10)
+SWEEP_METHODS = ("mpe", "rre", "svdmpe")
+
+
+def mk_sweep_study(torch, red, seeds=(0, 1, 2), methods=SWEEP_METHODS, ms=SWEEP_M,
+                   kappas=SWEEP_KAPPA):
+    """Robustness to m and kappa (Sec. IV-C, Fig. 4 (a)-(c)) on x3 super-resolution of
+    256x256 images: for every (m, kappa) of the grid, the denoiser calls Algorithm 3 needs
+    to reach plain FP's objective after 200 calls, and its objective after 200 calls as a
+    fraction of plain FP's; Fig. 4 (d): the best pair of the grid for MPE, RRE and SVD-MPE.
+    kappa is the paper's (kappa + 1 FP steps per cycle after the m lead-in steps, so the
+    library's ve_k = kappa + 1)."""
+    from paper_1805_02158_gb300 import synth
+    problems = [synth.sr_x3(s) for s in seeds]
+    ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
+    x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in problems]
+    outs = [torch.empty_like(x) for x in x0s]
+    psnr_fp, e_fp = _fp_reference(problems, ys, x0s, outs, red)
+    grid, best = {}, {}
+    for method in methods:
+        for m in ms:
+            for kappa in kappas:
+                VP = [red.Problem(red.config_for(p, ve=method, ve_k=kappa + 1, ve_m=m), y)
+                      for p, y in zip(problems, ys)]
+                need_cost, _, ratio = _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp,
+                                                      final_objective=True)
+                row = {"calls_to_fp200_cost": need_cost,
+                       "cost_reached": sum(c is not None for c in need_cost),
+                       "cost_calls_mean_reached": _mean_reached(need_cost),
+                       "objective_at_200_over_fp": ratio}
+                grid[f"{method}_m{m}_kappa{kappa}"] = row
+                key = (-row["cost_reached"], row["cost_calls_mean_reached"] or float(CALLS))
+                if method not in best or key < best[method][0]:
+                    best[method] = (key, {"m": m, "kappa": kappa, **row})
+                del VP
+    return {"task": "x3 SR, 256x256, 7x7 Gaussian std 1.6, noise sigma 5, CG 20",
+            "seeds": list(seeds), "fp_calls": CALLS, "fp200_objective": e_fp,
+            "grid": grid, "best_pair": {k: v[1] for k, v in best.items()}}
 
 
 def secondary_workloads(red, torch, flush, steps=3, warmup=3):
@@ -343,7 +403,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-study", action="store_true", help="skip the VE-vs-FP call study")
+    ap.add_argument("--no-study", action="store_true", help="skip the VE-vs-FP call studies and the (m, kappa) sweep")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer (0: none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
@@ -516,12 +576,13 @@ def main():
             print(f"bench: {type(e).__name__}: {e}", file=sys.stderr)
             return {"error": f"{type(e).__name__}: {e}"}
 
-    study = study_sr = None
+    study = study_sr = sweep = None
     if not args.no_study and rank == 0:
         from paper_1805_02158_gb300 import synth as _synth
         study = optional(lambda: ve_vs_fp_study(problems, Ps, torch, red))
         study_sr = optional(lambda: ve_vs_fp_study([_synth.sr_x3(i) for i in range(9)], None, torch,
                                                    red, (("mpe", 5), ("rre", 5))))
+        sweep = optional(lambda: mk_sweep_study(torch, red))
     secondary = None
     if not args.no_secondary and rank == 0:
         secondary = optional(lambda: secondary_workloads(red, torch, flush))
@@ -557,6 +618,7 @@ def main():
         "gpu_launches": int(launches),
         "ve_vs_fp": study,
         "ve_vs_fp_sr": study_sr,
+        "m_kappa_sweep_sr": sweep,
         "other_workloads": secondary,
         "serving": serving,
     }

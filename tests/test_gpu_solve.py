@@ -70,6 +70,26 @@ def test_sr_solve_matches_oracle():
     assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
 
 
+@pytest.mark.parametrize("method,m,kappa", [("mpe", 5, 3), ("mpe", 10, 10), ("rre", 0, 10),
+                                            ("svdmpe", 5, 5)])
+def test_sr_lead_in_and_window_grid_matches_oracle(method, m, kappa):
+    """Points of the (m, kappa) grid of Sec. IV-C (Fig. 4): m lead-in FP steps, a window of
+    kappa + 2 iterates (up to 12), one extrapolation, then 3 FP steps, on a 72x72 x3 SR
+    problem (LR 24x24) against the oracle. The image is chosen so that every extrapolation
+    is well conditioned (sum |gamma| <= 180, Eq. (21)), which keeps the FP32 rounding of the
+    iterates within the usual bars; MPE's PSNR bar is 0.02 dB as for the deblurring solves."""
+    p = synth.sr_x3(1, 72)
+    calls = m + kappa + 1 + 3
+    x_ref, st_ref = oracle_solve(p, method, kappa, calls, m=m)
+    x, st = gpu_solve(p, method, kappa + 1, calls, m=m)
+    assert st["fp_calls"] == calls
+    assert st["ve_steps"] == st_ref["ve_steps"] == 1
+    assert st["ve_breakdowns"] == st_ref["ve_breakdowns"] == 0
+    assert rel_l2(x, x_ref) <= 1e-3
+    bar = 0.02 if method in ("mpe", "svdmpe") else 0.01
+    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= bar
+
+
 def test_ve_beats_plain_fp_in_denoiser_calls():
     """VE reaches plain FP's objective after 100 calls with fewer calls (the criterion of
     Table I, Sec. IV). The objective is evaluated on the GPU (red_objective, itself checked
