@@ -16,7 +16,9 @@ Modules:
                 conjugate gradients for super-resolution (footnote to Eq. 7).
   ve         -- MPE (Algorithm 1) with MGS QR (Algorithm 2), RRE (Eq. 19) and SVD-MPE.
   red        -- the objective Eq. (4), PSNR, relative change and the cycling driver
-                (Algorithm 3).
+                (Algorithm 3), with full cycling or cycling with frozen gamma.
+  sd         -- the fixed-step steepest-descent baseline of SD-MPE (Sec. IV), a map of
+                one denoiser call per step that the same driver cycles.
 
 Pinning: every function is checked in tests/test_oracle_*.py against facts that do not
 come from the oracle itself (brute force, closed forms, dense solves, invariants).

@@ -11,14 +11,21 @@ Algorithm 3 (Sec. III-C), with these readings of what the paper leaves open:
     reached. The solve returns that FP iterate, so every extrapolated vector is followed
     by at least one FP step (the "additional iterations" remark of Sec. III-C);
   * on an extrapolation breakdown the next cycle starts from the last FP iterate.
-  * with method "none" the driver is the plain FP iteration of Eq. (7).
+  * with method "none" the driver is the plain FP iteration of Eq. (7);
+  * cycling with frozen gamma (a remark of Sec. III-C; the paper leaves its details to the
+    VE literature): after `freeze_after` cycles whose extrapolation succeeded, every later
+    cycle runs m + kappa baseline steps and combines x_m .. x_{m+kappa} with the last
+    computed gamma by Eq. (11), without the QR and the gamma solve (x_{m+kappa+1} is only
+    needed to form U for the solve); before that, cycles are full;
+  * the baseline map F may be any map of one denoiser call per step: the FP map of
+    Eq. (7) (fp.FPOperator) or the steepest-descent step of SD-MPE (sd.SDOperator).
 """
 from __future__ import annotations
 
 import numpy as np
 
 from . import operators as ops
-from .ve import extrapolate
+from .ve import combine_direct, extrapolate
 
 
 def objective(x: np.ndarray, fx: np.ndarray, y: np.ndarray, otf: np.ndarray, scale: int,
@@ -44,15 +51,18 @@ def rel_change(x_new: np.ndarray, x_old: np.ndarray) -> float:
 
 
 def solve(F, x0: np.ndarray, method: str = "none", m: int = 0, kappa: int = 4,
-          max_calls: int = 200, tol: float = 0.0, callback=None):
-    """Algorithm 3 around the FP map F. Returns (x, stats). `callback(calls, x)` is called
-    after every FP step (for convergence studies)."""
+          max_calls: int = 200, tol: float = 0.0, callback=None, freeze_after=None):
+    """Algorithm 3 around the baseline map F. Returns (x, stats). `callback(calls, x)` is
+    called after every baseline step (for convergence studies). `freeze_after`: None for
+    full cycling, else the number of successful full cycles after which gamma is frozen."""
     x = np.asarray(x0, dtype=np.float64).copy()
     calls = 0
     stats = {"fp_calls": 0, "ve_steps": 0, "ve_breakdowns": 0, "gammas": [],
-             "sum_abs_gamma": [], "rel_change": None}
-    per_cycle = m + kappa + 1
+             "sum_abs_gamma": [], "rel_change": None, "frozen_steps": 0}
+    frozen = None
     while True:
+        # a frozen cycle needs x_m .. x_{m+kappa} only: x_{m+kappa+1} serves the gamma solve
+        per_cycle = m + kappa + (1 if frozen is None else 0)
         stored = [x] if (method != "none" and m == 0) else []
         for i in range(1, per_cycle + 1):
             x_new = F(x)
@@ -68,6 +78,11 @@ def solve(F, x0: np.ndarray, method: str = "none", m: int = 0, kappa: int = 4,
                 return x, stats
         if method == "none":
             continue
+        if frozen is not None:
+            x = combine_direct(stored, frozen)
+            stats["ve_steps"] += 1
+            stats["frozen_steps"] += 1
+            continue
         s, gamma, info = extrapolate(stored, method)
         stats["ve_steps"] += 1
         if s is None:
@@ -77,3 +92,5 @@ def solve(F, x0: np.ndarray, method: str = "none", m: int = 0, kappa: int = 4,
             stats["gammas"].append(gamma)
             stats["sum_abs_gamma"].append(info["sum_abs_gamma"])
             x = s
+            if freeze_after is not None and len(stats["gammas"]) >= freeze_after:
+                frozen = gamma
