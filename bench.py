@@ -128,42 +128,112 @@ def max_over_ranks(dist, x):
     return float(t.item())
 
 
-def cpu_oracle_sample(seconds_target=12.0):
-    """The FP64 oracle as it stands: Algorithm 3 (RRE, kappa = 4) on one 256x256 problem
-    of the workload for as many FP steps as fit in the target (>= 2)."""
+def _oracle_problem(seed):
     from oracle import fp as ofp
-    from oracle import red as ored
     from paper_1805_02158_gb300 import synth
-    p = synth.deblur_gauss256(0, SIDE)
+    p = synth.deblur_gauss256(seed, SIDE)
     y = p.y.astype(np.float32).astype(np.float64)
-    F = ofp.FPOperator(y, p.psf, (SIDE, SIDE), 1, p.sigma, p.alpha)
+    return ofp.FPOperator(y, p.psf, (SIDE, SIDE), 1, p.sigma, p.alpha), y
+
+
+def _oracle_warm(seed):
+    _oracle_problem(seed)
+
+
+def _oracle_solve_timed(task):
+    """One image of the workload through the oracle's Algorithm 3 (RRE, kappa = 4) for a
+    fixed number of FP steps; returns the system-wide monotonic start and end times."""
+    from oracle import red as ored
+    seed, calls = task
+    F, y = _oracle_problem(seed)
+    t0 = time.monotonic()
+    ored.solve(F, y, "rre", m=0, kappa=VE_K - 1, max_calls=calls)
+    return t0, time.monotonic()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_calls_for(seconds_target):
+    """FP steps of one oracle solve that take about `seconds_target` on one core (>= 2)."""
+    F, y = _oracle_problem(0)
     t0 = time.perf_counter()
     F(y)
     one = time.perf_counter() - t0
-    calls = max(2, min(12, int(seconds_target / max(one, 1e-3))))
-    t0 = time.perf_counter()
-    ored.solve(F, y, "rre", m=0, kappa=VE_K - 1, max_calls=calls)
-    dt = time.perf_counter() - t0
-    return {"value": SIDE * SIDE * calls / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 image 256x256, {calls} FP steps of RRE k=5 (Algorithm 3), FP64 NumPy, "
-                      f"{dt:.1f} s"}
+    return max(2, min(12, int(seconds_target / max(one, 1e-3))))
+
+
+def cpu_oracle_sample(seconds_target=12.0, pool=None, workers=1, calls=None):
+    """The FP64 oracle as it stands on the host cores: `workers` images of the workload
+    (seeds 0..workers-1), one process each (NumPy single-threaded), each running Algorithm 3
+    (RRE, kappa = 4) for as many FP steps as take about `seconds_target` on one core.
+    Throughput = all images' pixels x FP steps / (last end - first start)."""
+    calls = calls or oracle_calls_for(seconds_target)
+    tasks = [(seed, calls) for seed in range(workers)]
+    spans = pool.map(_oracle_solve_timed, tasks) if pool is not None else \
+        [_oracle_solve_timed(t) for t in tasks]
+    dt = max(b for _, b in spans) - min(a for a, _ in spans)
+    return {"value": workers * SIDE * SIDE * calls / dt / 1e6, "unit": UNIT, "cores": workers,
+            "kind": "oracle",
+            "sample": f"{workers} image(s) 256x256 in {workers} process(es), {calls} FP steps "
+                      f"each of RRE k=5 (Algorithm 3), FP64 NumPy, {dt:.1f} s"}
+
+
+def oracle_pool(workers):
+    """A process pool for the oracle. Spawned (not forked): the parent may already hold a
+    CUDA context."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers) if workers > 1 else None
+
+
+def cpu_baseline_all_cores(seconds_target=12.0):
+    """The oracle timed on one core and on all host cores (one image per core, up to the
+    workload's 10 images)."""
+    calls = oracle_calls_for(seconds_target)
+    single = cpu_oracle_sample(seconds_target, calls=calls)
+    workers = min(host_cores(), N_IMAGES)
+    pool = oracle_pool(workers)
+    try:
+        if pool is not None:
+            pool.map(_oracle_warm, range(workers))        # start-up and imports, untimed
+        out = cpu_oracle_sample(seconds_target, pool, workers, calls)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    out["single_core"] = {"value": single["value"], "cores": 1, "sample": single["sample"]}
+    return out
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    workers = min(host_cores(), N_IMAGES)
+    calls = oracle_calls_for(4.0)
+    pool = oracle_pool(workers)
     steps = []
-    for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(seconds_target=4.0)
-        if i >= args.warmup:
-            steps.append(r)
+    try:
+        if pool is not None:
+            pool.map(_oracle_warm, range(workers))
+        for i in range(args.warmup + args.steps):
+            r = cpu_oracle_sample(4.0, pool, workers, calls)
+            if i >= args.warmup:
+                steps.append(r)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
     value = float(np.mean([s["value"] for s in steps]))
     calls_ms = 1e3 * SIDE * SIDE * CALLS * N_IMAGES / (value * 1e6)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": calls_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                              "sample": steps[-1]["sample"] + " per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -594,7 +664,7 @@ def main():
         if dist:
             dist.barrier()
         return
-    cpu = None if args.no_cpu else optional(cpu_oracle_sample)
+    cpu = None if args.no_cpu else optional(cpu_baseline_all_cores)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
