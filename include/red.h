@@ -75,8 +75,8 @@ typedef struct {
                          /* squared patch difference)                                    */
   int ve;                /* red_ve                                                      */
   int ve_k;              /* FP steps per cycle = columns of U = kappa + 1 (1..12)        */
-  int ve_m;              /* lead-in FP steps per cycle before the stored window (>= 0)   */
-  int cg_iters;          /* CG iterations per FP step for SR (e.g. 20)                   */
+  int ve_m;              /* lead-in FP steps per cycle before the stored window (0..64)  */
+  int cg_iters;          /* CG iterations per FP step for SR (0..1000; default 20)       */
   int storage;           /* red_dtype of the iterate history (F32 or BF16)               */
 } red_config;
 
