@@ -106,3 +106,20 @@ def test_objective_gradient_and_value_with_a_linear_denoiser(make):
         assert abs(num - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
     assert e(np.zeros(shape)) == pytest.approx(float(np.vdot(p.y, p.y)) / (2 * p.sigma ** 2),
                                                rel=1e-12)
+
+
+def test_breakdown_continues_from_the_last_fp_iterate():
+    """Reading: when an extrapolation does not exist the next cycle starts from the last FP
+    iterate. A constant drift x -> x + c (all differences equal, so U has rank 1 and every
+    extrapolation breaks down) must then advance by c at every call, as plain FP does."""
+    c = np.linspace(0.5, 2.0, 6)
+
+    class Drift:
+        def __call__(self, x):
+            return x + c
+
+    x0 = np.ones(6)
+    for method in ["mpe", "rre", "svdmpe"]:
+        x, st = red.solve(Drift(), x0, method, m=1, kappa=3, max_calls=13)
+        assert st["fp_calls"] == 13 and st["ve_steps"] == 2 and st["ve_breakdowns"] == 2
+        np.testing.assert_allclose(x, x0 + 13 * c, rtol=1e-14)

@@ -195,3 +195,17 @@ def test_breakdown_on_zero_leading_difference():
     for method in ["mpe", "rre", "svdmpe"]:
         x, g, info = ve.extrapolate(xs, method)
         assert x is None and info["breakdown"] and 0 in info["rank_deficient"]
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e3, 1e-3])
+def test_rank_loss_threshold_is_relative(scale):
+    """Reading of the rank-loss rule: column i of U is dependent iff r_ii^2 <= 1e-12 |u_i|^2,
+    a test on the relative remainder, unchanged by scaling U. A remainder of 1e-7 of the
+    column (1e-14 squared) is dependent, one of 1e-5 (1e-10 squared) is not."""
+    e1, e2, e3 = np.eye(3)
+    for delta, dependent in [(1e-7, True), (1e-5, False)]:
+        U = scale * np.stack([e1, e1 + delta * e2, e3], axis=1)
+        Q, R = ve.mgs_qr(U)
+        assert R[1, 1] == pytest.approx(scale * delta, rel=1e-6)
+        assert (1 in ve.rank_deficient_columns(U, R)) is dependent
+        assert 0 not in ve.rank_deficient_columns(U, R) and 2 not in ve.rank_deficient_columns(U, R)
