@@ -137,3 +137,46 @@ def test_cg_energy_error_decreases():
         errs.append(float(e @ A @ e))
     assert all(errs[i + 1] <= errs[i] * (1 + 1e-12) for i in range(len(errs) - 1))
     assert errs[-1] < 1e-6 * errs[0]
+
+
+def test_deblur_solve_with_an_asymmetric_psf_equals_dense_solve():
+    """A non-symmetric PSF has a complex spectrum, so the conjugate in H^T of Eq. (7)
+    matters (the paper's PSFs are symmetric and real-spectrum; the solve is defined for any
+    circulant H)."""
+    rng = np.random.default_rng(7)
+    psf = rng.uniform(0, 1, (3, 5))
+    psf /= psf.sum()
+    h, w, sigma, alpha = 6, 10, 1.5, 0.1
+    y = rng.uniform(0, 255, (h, w))
+    f = rng.uniform(0, 255, (h, w))
+    M = dense_blur_matrix(psf, h, w)
+    A = M.T @ M / sigma ** 2 + alpha * np.eye(h * w)
+    x_dense = np.linalg.solve(A, M.T @ y.ravel() / sigma ** 2 + alpha * f.ravel())
+    x = fp.deblur_solve(f, y, ops.psf_otf(psf, (h, w)), sigma, alpha)
+    np.testing.assert_allclose(x.ravel(), x_dense, rtol=1e-10, atol=1e-9)
+
+
+def test_sr_fp_step_warm_starts_cg_at_the_current_iterate():
+    """Reading: CG starts from x_k. With 0 iterations the SR FP step returns x_k; with one
+    it is the exact line-search step from x_k along r = b - A x_k, x_k + (r^T r / r^T A r) r,
+    written here with the dense A and b."""
+    h = w = 12
+    s, sigma, alpha = 3, 5.0, 0.02
+    psf = synth.gaussian_psf(7, 1.6)
+    B = dense_blur_matrix(psf, h, w)
+    S = dense_decimation(h, w, s)
+    A = (S @ B).T @ (S @ B) / sigma ** 2 + alpha * np.eye(h * w)
+    rng = np.random.default_rng(8)
+    y = rng.uniform(0, 255, (h // s, w // s))
+    xk = rng.uniform(0, 255, (h, w))
+    F0 = fp.FPOperator(y, psf, (h, w), s, sigma, alpha, cg_iters=0)
+    np.testing.assert_array_equal(F0(xk), xk)
+    F1 = fp.FPOperator(y, psf, (h, w), s, sigma, alpha, cg_iters=1)
+    x1, f = F1.step_with_f(xk)
+    b = (S @ B).T @ y.ravel() / sigma ** 2 + alpha * f.ravel()
+    r = b - A @ xk.ravel()
+    expect = xk.ravel() + (r @ r) / (r @ A @ r) * r
+    np.testing.assert_allclose(x1.ravel(), expect, rtol=1e-10, atol=1e-8)
+    # the module-level step takes the same path
+    np.testing.assert_allclose(fp.sr_fp_step(xk, y, ops.psf_otf(psf, (h, w)), s, sigma, alpha,
+                                             cg_iters=1), x1, rtol=1e-13, atol=1e-10)
