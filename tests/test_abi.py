@@ -63,6 +63,15 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(task="sr", scale=1), red.RED_EINVAL),
     (dict(ve=7), red.RED_EINVAL),                          # no such method
     (dict(storage="f16"), red.RED_EUNSUPPORTED),
+    (dict(ve_k=0), red.RED_EINVAL),                        # no U column
+    (dict(ve_m=65), red.RED_EINVAL),                       # lead-in above 64
+    (dict(ve_m=-1), red.RED_EINVAL),
+    (dict(cg_iters=1001), red.RED_EINVAL),
+    (dict(alpha=0.0), red.RED_EINVAL),                     # Eq. (4) needs alpha > 0
+    (dict(nlm_h=0.0), red.RED_EINVAL),
+    (dict(psf=np.ones((4, 4)) / 16), red.RED_EINVAL),      # even PSF: no centre tap
+    (dict(height=8, width=8, psf=synth.uniform_psf(9)), red.RED_EINVAL),   # PSF > image
+    (dict(height=4096, width=4096), red.RED_EINVAL),       # above the 2048 side limit
 ])
 def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
     base = dict(height=64, width=64, psf=synth.uniform_psf(9))
