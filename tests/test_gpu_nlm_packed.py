@@ -50,6 +50,9 @@ print(json.dumps({"ok": True}))
 def run_child(tmp, packed):
     env = dict(os.environ)
     env.pop("RED_NLM_F32X2", None)
+    # one tuning cache for both processes: the same launch shapes (the Fourier paths agree
+    # only to rounding, so a different autotuned choice would break bit equality)
+    env["RED_TUNE_CACHE"] = str(tmp.parent / "tune_cache.txt")
     if packed:
         env["RED_NLM_F32X2"] = "1"
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(tmp)], env=env, capture_output=True,
