@@ -196,15 +196,8 @@ __device__ __forceinline__ f2 pk(float lo, float hi) {
   asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
   return r;
 }
-__device__ __forceinline__ float lo_of(f2 v) {
-  float lo, hi;
+__device__ __forceinline__ void up(f2 v, float &lo, float &hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-  return lo;
-}
-__device__ __forceinline__ float hi_of(f2 v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-  return hi;
 }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
   f2 d;
@@ -314,14 +307,16 @@ k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int 
           const f2 e = sub2(b[r - 1 + dyi], a[r - 1]);   // = -d[r - 1], exactly
           v = fma2(d[r + 4], d[r + 4], fma2(e, d[r - 1], v));
         }
-        const float v0 = lo_of(v), v1 = hi_of(v);
+        float v0, v1;
+        up(v, v0, v1);
         const float p = v0 + v1;
         const float pl = __shfl_up_sync(kFull, p, 1);
         const float pr = __shfl_down_sync(kFull, p, 1);
         const float v1l = __shfl_up_sync(kFull, v1, 1);
         const float v0r = __shfl_down_sync(kFull, v0, 1);
-        const f2 D = add2(add2(pk(pl, v1l), pk(p, p)), pk(v0r, pr));
-        const f2 w = pk(ex2_approx(-lo_of(D)), ex2_approx(-hi_of(D)));
+        float D0, D1;
+        up(add2(add2(pk(pl, v1l), pk(p, p)), pk(v0r, pr)), D0, D1);
+        const f2 w = pk(ex2_approx(-D0), ex2_approx(-D1));
         num[r] = fma2(w, b[r + 2 + dyi], num[r]);
         den[r] = add2(den[r], w);
       }
@@ -336,8 +331,11 @@ k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int 
   for (int r = 0; r < R; ++r) {
     const int gr = tr0 + r;
     if (gr >= H) break;
-    if (c < W) dst[(long)gr * W + c] = (lo_of(num[r]) / lo_of(den[r])) * inv_k;
-    if (c + 1 < W) dst[(long)gr * W + c + 1] = (hi_of(num[r]) / hi_of(den[r])) * inv_k;
+    float n0, n1, d0, d1;
+    up(num[r], n0, n1);
+    up(den[r], d0, d1);
+    if (c < W) dst[(long)gr * W + c] = (n0 / d0) * inv_k;
+    if (c + 1 < W) dst[(long)gr * W + c + 1] = (n1 / d1) * inv_k;
   }
 }
 
