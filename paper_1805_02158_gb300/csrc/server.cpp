@@ -27,6 +27,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iomanip>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -65,6 +66,7 @@ struct Request {
 
 std::string key_of(const red_config &c, const std::vector<float> &psf) {
   std::ostringstream o;
+  o << std::setprecision(17);   // sigma, alpha and h round-trip: equal keys, equal physics
   o << c.task << "|" << c.height << "x" << c.width << "|" << c.scale << "|" << c.psf_h << "x"
     << c.psf_w << "|" << c.sigma << "|" << c.alpha << "|" << c.nlm_h << "|" << c.ve << "|"
     << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|";
