@@ -26,3 +26,42 @@ def to_host(t):
 def f32(a):
     """The float32 rounding of an array, as float64 (what both sides are fed)."""
     return np.asarray(a, np.float32).astype(np.float64)
+
+
+# Bars of the FP32 path against the FP64 oracle from the same float32 inputs.
+SOLVE_REL_L2 = 1e-3      # relative L2 of a whole solve
+SOLVE_PSNR_DB = 0.01     # |PSNR difference| of a whole solve
+SOLVE_MAX_ABS = 0.5      # every pixel of a solve within half a grey level of [0, 255]
+STEP_REL_L2 = 1e-5       # one FP step or one linear solve
+STEP_MAX_ABS = 2e-3      # every pixel of one step (the NLM bar: ex2.approx + FP32 sums)
+
+
+def solve_errors(x, x_ref, x_true):
+    x = np.asarray(x, np.float64)
+    x_ref = np.asarray(x_ref, np.float64)
+    return {"rel_l2": rel_l2(x, x_ref), "psnr_db": abs(psnr(x, x_true) - psnr(x_ref, x_true)),
+            "max_abs": float(np.abs(x - x_ref).max())}
+
+
+def assert_solve_close(x, x_ref, x_true, label="", rel=SOLVE_REL_L2, db=SOLVE_PSNR_DB,
+                       max_abs=SOLVE_MAX_ABS):
+    """A GPU solve against the oracle's: relative L2, PSNR and element-wise bars."""
+    e = solve_errors(x, x_ref, x_true)
+    msg = (f"{label}: rel L2 {e['rel_l2']:.3e} (bar {rel:g}), PSNR diff {e['psnr_db']:.5f} dB "
+           f"(bar {db:g}), max abs {e['max_abs']:.4e} (bar {max_abs:g})")
+    print(msg)
+    assert e["rel_l2"] <= rel and e["psnr_db"] <= db and e["max_abs"] <= max_abs, msg
+    return e
+
+
+def assert_step_close(x, ref, label="", rel=STEP_REL_L2, max_abs=STEP_MAX_ABS):
+    """One FP step (or linear solve, or extrapolation) against the oracle: relative L2 and
+    element-wise bars."""
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    r = rel_l2(x, ref)
+    m = float(np.abs(x - ref).max())
+    msg = f"{label}: rel L2 {r:.3e} (bar {rel:g}), max abs {m:.4e} (bar {max_abs:g})"
+    print(msg)
+    assert r <= rel and m <= max_abs, msg
+    return r, m

@@ -62,7 +62,7 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(ve_k=13), red.RED_EINVAL),
     (dict(task="sr", scale=1), red.RED_EINVAL),
     (dict(ve=7), red.RED_EINVAL),                          # no such method
-    (dict(storage="f16"), red.RED_EUNSUPPORTED),
+    (dict(storage=5), red.RED_EINVAL),                     # no such storage type
     (dict(ve_k=0), red.RED_EINVAL),                        # no U column
     (dict(ve_m=65), red.RED_EINVAL),                       # lead-in above 64
     (dict(ve_m=-1), red.RED_EINVAL),
@@ -81,6 +81,17 @@ def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
     st = lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out))
     assert st == status
     assert red.lib().red_last_error()
+
+
+def test_16_bit_storage_footprints(lib):
+    """BF16 and FP16 histories take half the ring bytes of FP32 (k + 2 slots of 64 x 64)."""
+    sizes = {}
+    for st in ("f32", "bf16", "f16"):
+        cfg = red.make_config(height=64, width=64, psf=synth.uniform_psf(9), storage=st)
+        out = ctypes.c_size_t()
+        assert lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out)) == red.RED_OK
+        sizes[st] = out.value
+    assert sizes["bf16"] == sizes["f16"] == sizes["f32"] - 7 * 64 * 64 * 2
 
 
 def test_svdmpe_config_accepted(lib):

@@ -2,17 +2,18 @@
 identical float32 inputs: the denoiser f (NLM), one FP step (Eq. (7)) for deblurring
 and super-resolution, and one extrapolation (Algorithm 1 / RRE).
 
-Tolerances (FP32 arithmetic on [0, 255] images):
+Tolerances (FP32 arithmetic on [0, 255] images), each an element-wise bar beside a norm
+bar, so a localised error (a wrong boundary row, a wrong halo) cannot hide in the norm:
   * NLM: max |f_gpu - f_oracle| <= 2e-3 (weights come from ex2.approx, rel. error ~2^-22,
     and patch distances summed in FP32; ~1e-5 of the value range) and rel. L2 <= 1e-5;
-  * one FP step: rel. L2 <= 1e-5 (the per-step bound for FP32);
+  * one FP step (deblurring or SR): rel. L2 <= 1e-5 and max abs <= 2e-3;
   * extrapolation on the same vectors: gamma to 1e-6 relative when U is well
-    conditioned; output rel. L2 <= 1e-6.
+    conditioned; output rel. L2 <= 1e-6 and max abs <= 1e-3.
 """
 import numpy as np
 import pytest
 
-from helpers import f32, rel_l2, to_dev, to_host
+from helpers import assert_step_close, f32, rel_l2, to_dev, to_host
 from oracle import fp as ofp
 from oracle import nlm as onlm
 from oracle import operators as oops
@@ -99,7 +100,7 @@ def test_deblur_fp_step_matches_oracle(shape, psf):
     out = torch.empty(shape, device="cuda")
     P.fp_step(to_dev(x), out)
     ref = ofp.deblur_fp_step(x, f32(p.y), oops.psf_otf(p.psf, shape), p.sigma, p.alpha)
-    assert rel_l2(to_host(out), ref) <= 1e-5
+    assert_step_close(to_host(out), ref, f"deblur FP step {shape}")
 
 
 @pytest.mark.parametrize("path", ["0", "4", "16"])
@@ -115,7 +116,7 @@ def test_deblur_fp_step_both_fourier_paths(path, monkeypatch):
         out = torch.empty(shape, device="cuda")
         P.fp_step(to_dev(x), out)
         ref = ofp.deblur_fp_step(x, f32(p.y), oops.psf_otf(p.psf, shape), p.sigma, p.alpha)
-        assert rel_l2(to_host(out), ref) <= 1e-5
+        assert_step_close(to_host(out), ref, f"deblur FP step {shape}, cluster {path}")
 
 
 def test_fourier_paths_agree(monkeypatch):
@@ -130,8 +131,8 @@ def test_fourier_paths_agree(monkeypatch):
         out = torch.empty((96, 128), device="cuda")
         P.fp_step(to_dev(f32(p.y)), out)
         outs[path] = to_host(out)
-    assert rel_l2(outs["4"], outs["16"]) <= 1e-6
-    assert rel_l2(outs["0"], outs["16"]) <= 1e-6
+    assert_step_close(outs["4"], outs["16"], "cluster 4 vs 16", rel=1e-6, max_abs=1e-3)
+    assert_step_close(outs["0"], outs["16"], "three passes vs cluster 16", rel=1e-6, max_abs=1e-3)
 
 
 def test_deblur_fp_step_large_uses_three_passes():
@@ -148,7 +149,7 @@ def test_deblur_fp_step_large_uses_three_passes():
     out = torch.empty(shape, device="cuda")
     P.fp_step(x, out)
     ref = ofp.deblur_solve(to_host(f), f32(p.y), oops.psf_otf(p.psf, shape), p.sigma, p.alpha)
-    assert rel_l2(to_host(out), ref) <= 1e-5
+    assert_step_close(to_host(out), ref, "1024^2 three-pass solve")
 
 
 def test_deblur_linear_solve_alone_matches_closed_form():
@@ -162,7 +163,7 @@ def test_deblur_linear_solve_alone_matches_closed_form():
     out = torch.empty((96, 128), device="cuda")
     P.fp_step(to_dev(c), out)
     ref = ofp.deblur_solve(c, f32(p.y), oops.psf_otf(p.psf, (96, 128)), p.sigma, p.alpha)
-    assert rel_l2(to_host(out), ref) <= 1e-5
+    assert_step_close(to_host(out), ref, "linear solve alone")
 
 
 @pytest.mark.parametrize("cluster", ["8", "16"])
@@ -178,7 +179,7 @@ def test_sr_fp_step_matches_oracle(shape, cluster, monkeypatch):
     out = torch.empty((h, w), device="cuda")
     P.fp_step(to_dev(x), out)
     ref = ofp.sr_fp_step(x, f32(p.y), oops.psf_otf(p.psf, (h, w)), 3, p.sigma, p.alpha, 20)
-    assert rel_l2(to_host(out), ref) <= 1e-4
+    assert_step_close(to_host(out), ref, f"SR FP step {shape}, cluster {cluster}")
 
 
 @pytest.mark.parametrize("side,cluster", [(256, "8"), (256, "16"), (1024, "16"), (384, "8")])
@@ -197,7 +198,7 @@ def test_sr_linear_solve_alone_at_full_size(side, cluster, monkeypatch):
     P.fp_step(to_dev(c), out)
     ref = ofp.sr_fp_step(c, f32(p.y), oops.psf_otf(p.psf, (side, side)), 3, p.sigma, p.alpha, 20,
                          denoise=lambda v: v)
-    assert rel_l2(to_host(out), ref) <= 1e-4
+    assert_step_close(to_host(out), ref, f"SR CG alone {side}^2, cluster {cluster}")
 
 
 def fp_history(p, n, kappa_plus_2):
@@ -219,7 +220,7 @@ def test_extrapolation_on_fp_history(method):
     x_ref, g_ref, info = ove.extrapolate(xs, method)
     assert st == red.RED_OK and not info["breakdown"]
     np.testing.assert_allclose(gamma, g_ref, rtol=1e-6, atol=1e-9)
-    assert rel_l2(to_host(out), x_ref) <= 1e-6
+    assert_step_close(to_host(out), x_ref, f"{method} on FP history", rel=1e-6, max_abs=1e-3)
 
 
 @pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
@@ -243,7 +244,7 @@ def test_extrapolation_exact_on_linear_map(method):
     x_ref, g_ref, _ = ove.extrapolate(xs32, method)
     assert st == red.RED_OK
     np.testing.assert_allclose(gamma, g_ref, rtol=1e-5, atol=1e-8)
-    assert rel_l2(to_host(out), x_ref) <= 1e-6
+    assert_step_close(to_host(out), x_ref, f"{method} on a linear map", rel=1e-6, max_abs=1e-3)
 
 
 def test_extrapolation_breakdown_reported():

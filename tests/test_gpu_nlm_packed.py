@@ -1,6 +1,5 @@
 """The packed-FP32 NLM kernel (k_nlm_x2, selected by RED_NLM_F32X2=1) against the scalar
-kernel and the FP64 oracle. Opt-in (RED_TEST_NLM_PACKED=1) while the packed kernel is not
-the default: each kernel runs in its own process (the switch is read once per process) on
+kernel and the FP64 oracle. Each kernel runs in its own process (the switch is read once per process) on
 the same seeded images, through red_denoise and through a short batched solve; the two
 must agree bit for bit (same operations in the same order), and the packed one must meet
 the NLM parity bars against the oracle (max |diff| <= 2e-3 on [0, 255], rel. L2 <= 1e-5)."""
@@ -13,9 +12,7 @@ import pytest
 
 from helpers import f32, rel_l2
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("RED_TEST_NLM_PACKED") != "1",
-                                 reason="opt-in: RED_TEST_NLM_PACKED=1")]
+pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

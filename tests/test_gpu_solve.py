@@ -1,13 +1,14 @@
 """End-to-end parity of full RED solves (Algorithm 3 around Eq. (7)) on the GPU against
 the FP64 oracle, through the C-ABI, on seeded synthetic problems.
 
-Acceptance for FP32 solves: relative L2 <= 1e-3 and |PSNR difference| <= 0.01 dB against
-the oracle's solve from the same float32 inputs. Batches must reproduce single-problem
-solves exactly (fixed work decomposition, no atomics in any reduction)."""
+Acceptance for FP32 solves, for every extrapolation method: relative L2 <= 1e-3,
+|PSNR difference| <= 0.01 dB and every pixel within 0.5 grey levels of the oracle's solve
+from the same float32 inputs (helpers.assert_solve_close). Batches must reproduce
+single-problem solves exactly (fixed work decomposition, no atomics in any reduction)."""
 import numpy as np
 import pytest
 
-from helpers import f32, psnr, rel_l2, to_dev, to_host
+from helpers import assert_solve_close, f32, psnr, rel_l2, solve_errors, to_dev, to_host
 from oracle import fp as ofp
 from oracle import red as ored
 from paper_1805_02158_gb300 import red, synth
@@ -32,10 +33,9 @@ def gpu_solve(p, method, k, calls, tol=0.0, m=0, storage="f32", cg_iters=20):
 
 @pytest.mark.parametrize("method", ["none", "rre", "mpe", "svdmpe"])
 def test_deblur_64_solve_matches_oracle(method):
-    """Bars: relative L2 <= 1e-3, objective (Eq. (4), evaluated by the oracle) within 1e-4
-    relative, PSNR within 0.01 dB. On this problem MPE's extrapolations are near
-    breakdown (sum |gamma| reaches ~800, the stability factor of Eq. (21)), which magnifies
-    FP32 rounding differences by that factor; its PSNR bar is 0.02 dB."""
+    """The solve bars, and the objective (Eq. (4), evaluated by the oracle) within 1e-4
+    relative. On this problem MPE's extrapolations come close to breakdown (sum |gamma|
+    reaches ~800, the stability factor of Eq. (21))."""
     from oracle.nlm import nlm
     p = synth.deblur_small(0)
     x_ref, st_ref = oracle_solve(p, method, 4, 50)
@@ -43,13 +43,11 @@ def test_deblur_64_solve_matches_oracle(method):
     assert st["fp_calls"] == 50
     if method != "none":
         assert st["ve_steps"] == 9 and st_ref["ve_steps"] == 9
-    assert rel_l2(x, x_ref) <= 1e-3
+    assert_solve_close(x, x_ref, p.x_true, f"64^2 deblur {method}")
     F = ofp.FPOperator(f32(p.y), p.psf, (64, 64), 1, p.sigma, p.alpha)
     e = ored.objective(x, nlm(x), F.y, F.otf, 1, p.sigma, p.alpha)
     e_ref = ored.objective(x_ref, nlm(x_ref), F.y, F.otf, 1, p.sigma, p.alpha)
     assert abs(e - e_ref) <= 1e-4 * abs(e_ref)
-    bar = 0.02 if method in ("mpe", "svdmpe") else 0.01
-    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= bar
 
 
 def test_deblur_nonsquare_radix3_rre_m1():
@@ -57,8 +55,7 @@ def test_deblur_nonsquare_radix3_rre_m1():
     x_ref, _ = oracle_solve(p, "rre", 2, 23, m=1)
     x, st = gpu_solve(p, "rre", 3, 23, m=1)
     assert st["fp_calls"] == 23
-    assert rel_l2(x, x_ref) <= 1e-3
-    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+    assert_solve_close(x, x_ref, p.x_true, "48x72 deblur rre m=1")
 
 
 def test_sr_solve_matches_oracle():
@@ -66,28 +63,28 @@ def test_sr_solve_matches_oracle():
     x_ref, _ = oracle_solve(p, "rre", 4, 15)
     x, st = gpu_solve(p, "rre", 5, 15)
     assert st["fp_calls"] == 15
-    assert rel_l2(x, x_ref) <= 1e-3
-    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+    assert_solve_close(x, x_ref, p.x_true, "48^2 SR rre")
 
 
 @pytest.mark.parametrize("method,m,kappa", [("mpe", 5, 3), ("mpe", 10, 10), ("rre", 0, 10),
                                             ("svdmpe", 5, 5)])
 def test_sr_lead_in_and_window_grid_matches_oracle(method, m, kappa):
     """Points of the (m, kappa) grid of Sec. IV-C (Fig. 4): m lead-in FP steps, a window of
-    kappa + 2 iterates (up to 12), one extrapolation, then 3 FP steps, on a 72x72 x3 SR
-    problem (LR 24x24) against the oracle. The image is chosen so that every extrapolation
-    is well conditioned (sum |gamma| <= 180, Eq. (21)), which keeps the FP32 rounding of the
-    iterates within the usual bars; MPE's PSNR bar is 0.02 dB as for the deblurring solves."""
-    p = synth.sr_x3(1, 72)
+    kappa + 2 iterates (up to 12), one extrapolation, then 3 FP steps, on two 72x72 x3 SR
+    problems (LR 24x24) against the oracle, to the solve bars."""
+    for seed in (0, 1):
+        _grid_point(synth.sr_x3(seed, 72), method, m, kappa)
+
+
+def _grid_point(p, method, m, kappa):
     calls = m + kappa + 1 + 3
     x_ref, st_ref = oracle_solve(p, method, kappa, calls, m=m)
     x, st = gpu_solve(p, method, kappa + 1, calls, m=m)
     assert st["fp_calls"] == calls
     assert st["ve_steps"] == st_ref["ve_steps"] == 1
     assert st["ve_breakdowns"] == st_ref["ve_breakdowns"] == 0
-    assert rel_l2(x, x_ref) <= 1e-3
-    bar = 0.02 if method in ("mpe", "svdmpe") else 0.01
-    assert abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true)) <= bar
+    assert_solve_close(x, x_ref, p.x_true, f"72^2 SR {method} m={m} kappa={kappa} "
+                       f"sum|gamma|={st['sum_abs_gamma']:.1f}")
 
 
 def test_ve_beats_plain_fp_in_denoiser_calls():
@@ -151,8 +148,7 @@ def test_batch_uneven_sizes_matches_oracle(path, monkeypatch):
     B.solve(x0s, outs, 16, 0.0)
     for p, o in zip(probs, outs):
         x_ref, _ = oracle_solve(p, "rre", 4, 16)
-        assert rel_l2(to_host(o), x_ref) <= 1e-3
-        assert abs(psnr(to_host(o), p.x_true) - psnr(x_ref, p.x_true)) <= 0.01
+        assert_solve_close(to_host(o), x_ref, p.x_true, f"uneven batch {p.height}x{p.width}")
 
 
 def test_batch_host_buffers_match_device_path():
@@ -171,16 +167,36 @@ def test_batch_host_buffers_match_device_path():
         np.testing.assert_array_equal(to_host(a), b.numpy())
 
 
-def test_bf16_storage_error_is_reported():
+# 16-bit storage bounds for a 10-step 48x48 SR solve: BF16 keeps 8 significant bits (one
+# rounding is up to 0.5 at values in [128, 256)), FP16 11 bits (up to 0.0625 there); the
+# bounds let the rounding of every stored iterate accumulate over the solve.
+STORAGE_BOUNDS_48 = {"bf16": (0.1, 8.0), "f16": (0.02, 1.0)}
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_16_bit_storage_error_is_reported(storage):
     p = synth.sr_x3(1, 48)
     x_ref, _ = oracle_solve(p, "rre", 4, 10)
-    x, st = gpu_solve(p, "rre", 5, 10, storage="bf16")
+    x, st = gpu_solve(p, "rre", 5, 10, storage=storage)
     d_psnr = abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true))
     max_abs = float(np.abs(x - x_ref).max())
-    print(f"bf16 storage: PSNR error {d_psnr:.4f} dB, max-abs error {max_abs:.4f}")
-    # bf16 keeps 8 significant bits: one rounding is up to 0.5 at values in [128, 256);
-    # the bound allows the rounding of every stored iterate to accumulate over the solve
-    assert d_psnr <= 0.1 and max_abs <= 8.0
+    print(f"{storage} storage: PSNR error {d_psnr:.4f} dB, max-abs error {max_abs:.4f}")
+    db, ma = STORAGE_BOUNDS_48[storage]
+    assert d_psnr <= db and max_abs <= ma, (d_psnr, max_abs)
+
+
+def test_f16_storage_deblur_error_is_reported():
+    """FP16 storage on a deblurring solve (every kernel reads and writes the 16-bit ring).
+    Measured on GB300: 0.008 dB PSNR error and 3.0 max abs: this image's RRE weights reach
+    sum |gamma| ~ 10^2 (Eq. (21)), which magnifies the storage rounding (0.0625 at the top
+    of the range) at a few edge pixels; the bounds are twice the measured values."""
+    p = synth.deblur_small(4)
+    x_ref, _ = oracle_solve(p, "rre", 4, 30)
+    x, st = gpu_solve(p, "rre", 5, 30, storage="f16")
+    d_psnr = abs(psnr(x, p.x_true) - psnr(x_ref, p.x_true))
+    max_abs = float(np.abs(x - x_ref).max())
+    print(f"f16 storage, 64^2 deblur: PSNR error {d_psnr:.4f} dB, max-abs error {max_abs:.4f}")
+    assert st["fp_calls"] == 30 and d_psnr <= 0.02 and max_abs <= 6.0, (d_psnr, max_abs)
 
 
 def test_objective_matches_oracle():
@@ -215,9 +231,7 @@ def test_full_size_deblur_batch_matches_oracle():
     B.solve(x0s, outs, 30, 0.0)
     for i in (0, 7):
         x_ref, _ = oracle_solve(probs[i], "rre", 4, 30)
-        x = to_host(outs[i])
-        assert rel_l2(x, x_ref) <= 1e-3
-        assert abs(psnr(x, probs[i].x_true) - psnr(x_ref, probs[i].x_true)) <= 0.01
+        assert_solve_close(to_host(outs[i]), x_ref, probs[i].x_true, f"256^2 batch image {i}, 30 calls")
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
@@ -242,7 +256,7 @@ def test_full_size_sr_matches_oracle(storage):
     x = to_host(outs[1])
     d_psnr = abs(psnr(x, probs[1].x_true) - psnr(x_ref, probs[1].x_true))
     if storage == "f32":
-        assert rel_l2(x, x_ref) <= 1e-3 and d_psnr <= 0.01
+        assert_solve_close(x, x_ref, probs[1].x_true, "256^2 SR f32, 20 calls")
     else:
         max_abs = float(np.abs(x - x_ref).max())
         rel = rel_l2(x, x_ref)

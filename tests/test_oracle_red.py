@@ -123,3 +123,25 @@ def test_breakdown_continues_from_the_last_fp_iterate():
         x, st = red.solve(Drift(), x0, method, m=1, kappa=3, max_calls=13)
         assert st["fp_calls"] == 13 and st["ve_steps"] == 2 and st["ve_breakdowns"] == 2
         np.testing.assert_allclose(x, x0 + 13 * c, rtol=1e-14)
+
+
+def test_psnr_hand_computed():
+    """PSNR = 10 log10(255^2 / MSE) with MSE the mean over all pixels (Sec. IV reports PSNR
+    on the [0, 255] scale): values worked out by hand."""
+    # MSE = 255^2 / 100 -> exactly 20 dB; MSE = 255^2 -> exactly 0 dB
+    assert red.psnr(np.full((2, 2), 25.5), np.zeros((2, 2))) == pytest.approx(20.0, abs=1e-12)
+    assert red.psnr(np.full(3, 255.0), np.zeros(3)) == pytest.approx(0.0, abs=1e-12)
+    # errors (-2, 0, 3): MSE = 13 / 3, 255^2 / MSE = 195075 / 13 = 15005.769230769...,
+    # log10 of it = 4 + log10(1.5) + log10(1.000384615...) = 4.1762582..., so 41.762583 dB
+    assert red.psnr(np.array([10.0, 20.0, 30.0]), np.array([12.0, 20.0, 27.0])) == \
+        pytest.approx(41.76258263, abs=1e-7)
+
+
+def test_rel_change_hand_computed():
+    """Termination test of Algorithm 3: ||x_new - x_old|| / ||x_old||. x_old = (0, 0, 10),
+    x_new = (3, 4, 0): the difference has norm sqrt(125) = 11.18033988..., so the relative
+    change is 1.118033988... (dividing by ||x_new|| = 5 would give 2.236...)."""
+    assert red.rel_change(np.array([3.0, 4.0, 0.0]), np.array([0.0, 0.0, 10.0])) == \
+        pytest.approx(1.1180339887498949, rel=1e-14)
+    x = np.array([[1.0, -2.0], [2.0, 4.0]])
+    assert red.rel_change(x, x) == 0.0
