@@ -206,6 +206,7 @@ def cpu_baseline_all_cores(seconds_target=12.0):
             pool.close()
             pool.join()
     out["single_core"] = {"value": single["value"], "cores": 1, "sample": single["sample"]}
+    out["host_cores"] = host_cores()
     return out
 
 
@@ -234,9 +235,77 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "host_cores": host_cores(),
                              "sample": steps[-1]["sample"] + " per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_oracle():
+    """FP64 oracle solves at 200 FP steps, written by tests/golden/make_full_size_oracle.py
+    from oracle/ only (read here as data; no oracle code runs)."""
+    path = os.path.join(GOLDEN, "full_size_oracle.npz")
+    meta = os.path.join(GOLDEN, "full_size_oracle.json")
+    if not (os.path.exists(path) and os.path.exists(meta)):
+        return None, None
+    return np.load(path), json.load(open(meta))["cases"]
+
+
+def accuracy_vs_oracle(outs, problems, names, arrays):
+    """Errors of GPU results against the stored oracle solves of the same problems:
+    relative L2, |PSNR difference| (dB) and max abs, per image and worst."""
+    per = []
+    for o, p, name in zip(outs, problems, names):
+        if arrays is None or name not in arrays.files:
+            continue
+        x = o.detach().cpu().numpy().astype(np.float64)
+        ref = arrays[name].astype(np.float64)
+        d_psnr = abs(10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
+                     - 10 * math.log10(255 ** 2 / np.mean((ref - p.x_true) ** 2)))
+        per.append({"image": name, "rel_l2": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+                    "psnr_db": float(d_psnr), "max_abs": float(np.abs(x - ref).max())})
+    if not per:
+        return None
+    worst = {k: max(e[k] for e in per) for k in ("rel_l2", "psnr_db", "max_abs")}
+    return {"images_checked": len(per), "worst": worst, "per_image": per}
+
+
+def cufft_comparison(problems, torch, steps=200, reps=5):
+    """The Fourier-domain solve of Eq. (7) with library FFTs, timed for comparison only:
+    torch.fft (cuFFT) R2C of the ten f images, X = C + G F, C2R, over the same batch,
+    replayed from a CUDA graph (no host launch gaps); ms per FP step."""
+    n = len(problems)
+    f = torch.randn(n, SIDE, SIDE, device="cuda") * 40 + 128
+    C = torch.randn(n, SIDE, SIDE // 2 + 1, dtype=torch.complex64, device="cuda")
+    G = torch.rand(n, SIDE, SIDE // 2 + 1, device="cuda")
+    out = torch.empty_like(f)
+
+    def step():
+        out.copy_(torch.fft.irfft2(C + G * torch.fft.rfft2(f), s=(SIDE, SIDE)))
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            step()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(steps):
+                step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1) / steps)
+    return {"ms_per_fp_step": float(np.median(ms)), "batch": n,
+            "how": "torch.fft.rfft2 -> C + G*F -> irfft2 (cuFFT), CUDA graph of 200 steps"}
 
 
 STUDY_VARIANTS = (("rre", 5), ("mpe", 5), ("rre", 10), ("mpe", 10))
@@ -393,6 +462,11 @@ def secondary_workloads(red, torch, flush, steps=3, warmup=3):
                      "unit": UNIT, "ms_per_step": total / steps, "steps": steps, "warmup": warmup,
                      "solves_per_s": len(probs) * steps / (total / 1e3),
                      "launch_shapes": B.describe()}
+        if name.startswith("sr256"):
+            arrays, _ = stored_oracle()
+            acc = accuracy_vs_oracle(outs, probs, [f"sr256_rre_k5_s{i}" for i in range(len(probs))],
+                                     arrays)
+            out[name]["error_vs_fp64_oracle"] = acc if acc is not None else "stored oracle missing"
         del B, Ps
     return out
 
@@ -572,6 +646,19 @@ def main():
         vs_ms.append(B.phase_ms(red.PHASE_VESOLVE)[0])
     B.set_phase_timing(False)
 
+    # the timed solve's results (identical in every step) against the stored FP64 oracle
+    arrays, _ = stored_oracle()
+    accuracy = None
+    if rank == 0:
+        accuracy = accuracy_vs_oracle(outs, problems,
+                                      [f"deblur256_rre_k5_s{s}" for s in problem_seeds(rank)], arrays)
+        if accuracy is not None:
+            w = accuracy["worst"]
+            accuracy["within_bars"] = bool(w["rel_l2"] <= 1e-3 and w["psnr_db"] <= 0.01
+                                           and w["max_abs"] <= 0.5)
+            accuracy["bars"] = {"rel_l2": 1e-3, "psnr_db": 0.01, "max_abs": 0.5}
+            accuracy.pop("per_image")
+
     pix = SIDE * SIDE * N_IMAGES
     units = pix * CALLS * args.steps * world
     value = units / (total_ms / 1e3) / 1e6
@@ -604,6 +691,7 @@ def main():
         try:
             mu = red.measure_peaks()
             measured_units = {"fp32_fma_T_lane_ops": mu["fp32_fma"] / 1e12,
+                              "fp32x2_fma_T_lane_ops": mu["fp32x2_fma"] / 1e12,
                               "ex2_T_lane_ops": mu["ex2"] / 1e12,
                               "fp64_fma_T_lane_ops": mu["fp64_fma"] / 1e12,
                               "how": "independent FMA / ex2.approx chains on every SM (red_measure_peaks)"}
@@ -630,6 +718,12 @@ def main():
         "nlm": {"ms": float(np.mean(nlm_ms))},
         "hbm_peak_GBps": hbm,
     }
+    kern["fft_solve"]["frac_of_hbm_peak"] = kern["fft_solve"]["GBps"] / hbm
+    if rank == 0:
+        try:
+            kern["fft_solve"]["cufft_comparison"] = cufft_comparison(problems, torch)
+        except Exception as e:  # noqa: BLE001
+            kern["fft_solve"]["cufft_comparison"] = {"error": f"{type(e).__name__}: {e}"}
     traffic = None
     prof = os.path.join(ROOT, "profiles", "nlm_traffic.json")
     if os.path.exists(prof):
@@ -682,6 +776,7 @@ def main():
                      "measured_units": measured_units,
                      "step_ms_with_phase_events": float(np.mean(pstep_ms))},
         "kernels": kern,
+        "accuracy_vs_fp64_oracle": accuracy,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,

@@ -58,6 +58,12 @@ typedef enum { RED_VE_NONE = 0, RED_VE_MPE = 1, RED_VE_RRE = 2, RED_VE_SVDMPE = 
  * Gram matrix and gamma solve FP64-accurate. */
 typedef enum { RED_F32 = 0, RED_BF16 = 1, RED_F16 = 2 } red_dtype;
 
+/* Baseline map that Algorithm 3 cycles (one denoiser call per step, Sec. IV):
+ *   RED_BASE_FP: the fixed-point step of Eq. (7);
+ *   RED_BASE_SD: the fixed-step steepest descent x - mu grad E(x) on Eq. (5) (the
+ *                baseline of SD-MPE, Sec. IV-A/B). */
+typedef enum { RED_BASE_FP = 0, RED_BASE_SD = 1 } red_baseline;
+
 typedef struct {
   int task;              /* red_task                                                    */
   int height, width;     /* image (high-resolution) size; each must be 2^a * 3^b, width  */
@@ -77,7 +83,14 @@ typedef struct {
   int ve_k;              /* FP steps per cycle = columns of U = kappa + 1 (1..12)        */
   int ve_m;              /* lead-in FP steps per cycle before the stored window (0..64)  */
   int cg_iters;          /* CG iterations per FP step for SR (0..1000; default 20)       */
-  int storage;           /* red_dtype of the iterate history (F32 or BF16)               */
+  int storage;           /* red_dtype of the iterate history (F32, BF16 or F16)          */
+  int baseline;          /* red_baseline (default RED_BASE_FP)                           */
+  double sd_mu;          /* SD step size mu (RED_BASE_SD); 0 selects                     */
+                         /* 1 / (max |K(w)|^2 / sigma^2 + alpha), K the PSF spectrum     */
+  int ve_freeze;         /* cycling with frozen gamma (Sec. III-C remark): 0 = every     */
+                         /* cycle solves for gamma; n >= 1 = after n successful          */
+                         /* extrapolations, later cycles run ve_m + ve_k - 1 steps and   */
+                         /* combine with the last gamma (needs ve_m + ve_k >= 2)         */
 } red_config;
 
 typedef struct {
@@ -91,7 +104,8 @@ typedef struct {
 } red_stats;
 
 /* Fills `cfg` with the defaults used by the paper's deblurring experiments (Sec. IV-A):
- * NLM 5x5 / 11x11 / h = 10, alpha = 0.02, RRE with ve_k = 5, ve_m = 0, cg_iters = 20. */
+ * NLM 5x5 / 11x11 / h = 10, alpha = 0.02, RRE with ve_k = 5, ve_m = 0, cg_iters = 20,
+ * the FP baseline, no frozen gamma. */
 void red_config_default(red_config *cfg);
 
 /* ----------------------------------------------------------------------------------- */
@@ -261,11 +275,13 @@ red_status red_problem_footprint(const red_config *cfg, size_t *bytes);
 
 /* Measures the throughput of the arithmetic units the hot path is bound by, in lane
  * operations per second over the whole device: FP32 FMA (the NLM's arithmetic), the
- * ex2.approx special function (its weights) and FP64 FMA (the extrapolation solve), each by
- * independent dependency chains on every SM (a few ms; synchronises the stream). No
- * counterpart in the paper: it puts measured peaks beside the derived ones of the roofline. */
+ * ex2.approx special function (its weights), FP64 FMA (the extrapolation solve) and packed
+ * FP32 FMA (fma.rn.f32x2, two lane operations per instruction), each by independent
+ * dependency chains on every SM (a few ms; synchronises the stream). No counterpart in the
+ * paper: it puts measured peaks beside the derived ones of the roofline. */
 red_status red_measure_peaks(double *fp32_fma_lane_ops, double *ex2_lane_ops,
-                             double *fp64_fma_lane_ops, void *stream);
+                             double *fp64_fma_lane_ops, double *fp32x2_fma_lane_ops,
+                             void *stream);
 
 /* Number of kernel launches this library has issued in this process (for accounting). */
 uint64_t red_kernel_launches(void);

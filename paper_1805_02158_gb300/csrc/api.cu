@@ -75,7 +75,7 @@ static Layout layout_for(const red_config &c, int nslots, int slot_stride) {
   Layout L{};
   Carve cv;
   const size_t N = (size_t)c.height * c.width;
-  const size_t esz = c.storage == RED_BF16 ? 2 : 4;
+  const size_t esz = c.storage == RED_F32 ? 4 : 2;
   const size_t Wh = (size_t)c.width / 2 + 1;
   const size_t nchunks = (N + kGramChunk - 1) / kGramChunk;
   const bool sr = c.task == RED_SR;
@@ -131,8 +131,12 @@ static void validate(const red_config *c) {
   CHECK_ARG(c->cg_iters >= 0 && c->cg_iters <= 1000, "cg_iters must be in [0, 1000]");
   if (c->nlm_patch != 5 || c->nlm_search != 11)
     throw Fail{RED_EUNSUPPORTED, "only 5x5 patches and 11x11 search windows are supported"};
-  if (c->storage != RED_F32 && c->storage != RED_BF16)
-    throw Fail{RED_EUNSUPPORTED, "storage must be RED_F32 or RED_BF16"};
+  CHECK_ARG(c->storage == RED_F32 || c->storage == RED_BF16 || c->storage == RED_F16,
+            "storage must be RED_F32, RED_BF16 or RED_F16");
+  CHECK_ARG(c->baseline == RED_BASE_FP || c->baseline == RED_BASE_SD, "bad baseline");
+  CHECK_ARG(c->sd_mu >= 0.0 && c->ve_freeze >= 0, "sd_mu and ve_freeze must be >= 0");
+  if (c->baseline != RED_BASE_FP || c->ve_freeze != 0)
+    throw Fail{RED_EUNSUPPORTED, "the SD baseline and frozen gamma are not built yet"};
 }
 
 // ---------------------------------------------------------------------------------------
@@ -335,8 +339,8 @@ void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaS
 }
 
 // One FP step (Eq. (7)) over every problem of a plan.
-void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_bf16, cudaStream_t s) {
-  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_bf16, s,
+void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_type, cudaStream_t s) {
+  CUDA_OK(launch_nlm(d_probs, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, src_type, s,
                      nullptr, pl.lc.nlm_occ));
   launch_fft_solve(d_probs, pl, sa, s);
   if (pl.n_sr) CUDA_OK(launch_sr_step(d_probs, pl.d_sr, pl.n_sr, pl.lc.sr_cluster, pl.sr_cap, sa, s));
@@ -396,7 +400,7 @@ static void fill_prob_dev(red_problem_s *P) {
   d.scale = c.task == RED_SR ? c.scale : 1;
   d.lh = c.height / d.scale;
   d.lw = c.width / d.scale;
-  d.storage = c.storage == RED_BF16 ? 1 : 0;
+  d.storage = c.storage == RED_BF16 ? kStoreBF16 : (c.storage == RED_F16 ? kStoreF16 : kStoreF32);
   d.nslots = nslots_for(c);
   d.n_chunks = (d.N + kGramChunk - 1) / kGramChunk;
   d.kh = c.psf_h;

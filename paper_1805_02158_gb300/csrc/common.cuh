@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -19,6 +20,7 @@ constexpr double kSumTol = 1e-12;               // MPE existence: |sum c| > tol 
 
 enum Task { kDeblur = 0, kSR = 1 };
 enum Ve { kVeNone = 0, kVeMpe = 1, kVeRre = 2, kVeSvdMpe = 3 };
+enum Baseline { kBaseFP = 0, kBaseSD = 1 };   // the map Algorithm 3 cycles
 
 // Per-problem termination state, device resident; written by the step kernels.
 struct ProbState {
@@ -35,6 +37,11 @@ struct ProbState {
   double sum_abs_gamma;
   unsigned int counter;   // arrival counter for last-block reductions
   unsigned int counter2;
+  // cycling with frozen gamma (ProbDev::ve_freeze > 0)
+  int ve_ok;           // extrapolations that succeeded
+  int frozen;          // 1 once ve_ok reached ve_freeze: later cycles reuse xi
+  int solved;          // 1 between a gamma solve and the combine that uses it
+  int frozen_steps;    // combines with the frozen xi
 };
 
 // Everything a kernel needs to know about one problem. Plain data, copied to device
@@ -43,7 +50,7 @@ struct ProbDev {
   int H, W, M, Wh, N;     // image size; M = W/2; Wh = M + 1; N = H*W
   int slot_stride;        // elements between ring slots (multiple of 64)
   int task, scale, lh, lw;
-  int storage;            // 0 = f32 ring, 1 = bf16 ring
+  int storage;            // StoreType of the ring: 0 = f32, 1 = bf16, 2 = f16
   int nslots;
   int n_row_items;        // CTAs of one row-FFT launch for this problem
   int n_chunks;           // Gram / combine work units
@@ -51,9 +58,11 @@ struct ProbDev {
   int cg_iters;
   int ve_k;
   int ve_method;
+  int baseline;           // Baseline: FP step of Eq. (7) or SD step on Eq. (5)
+  int ve_freeze;          // 0, or freeze gamma after this many successful extrapolations
   float inv_sigma2, alpha;
   float nlm_k;            // NLM prescale sqrt(log2(e) / (P^2 h^2))
-  void *ring;             // nslots * slot_stride elements (float or bf16)
+  void *ring;             // nslots * slot_stride elements (float, bf16 or half)
   float *f;               // denoiser output, N
   float2 *spec;           // H x Wh half spectrum workspace (deblur)
   const float2 *Kh;       // H x Wh: K, the PSF spectrum (for H x in the objective)
@@ -67,6 +76,9 @@ struct ProbDev {
   const float *b0;        // H^T y / sigma^2 (N)
   float *cg_x, *cg_r, *cg_p, *cg_ap, *cg_z;   // CG vectors; z is LR sized
   const float *psf;       // kh x kw taps
+  // steepest descent (baseline kBaseSD): (mu, mu * alpha), computed on the device
+  float2 *sd;
+  unsigned int *sd_kmax;  // bits of max |K(w)|^2 (non-negative floats order as integers)
   // extrapolation
   double *gram_part;      // n_chunks x kMaxPairs
   double *ve_coef;        // kMaxK: xi_j of Algorithm 1 step 3 (difference form), + gamma
@@ -85,6 +97,7 @@ struct StepArgs {
   const void *src_ptr;    // if non-null: read this instead of slot src (f32)
   float *dst_ptr;         // if non-null: write this instead of slot dst (f32)
   int update_state;       // 1: batched solve step (skip done problems, count calls)
+  int skip_frozen;        // 1: the last step of a full cycle (skipped by frozen problems)
 };
 
 struct VeArgs {
@@ -94,6 +107,7 @@ struct VeArgs {
   int out_slot;
   int nvec;               // k + 1
   int update_state;
+  int skip_frozen;        // 1: Gram and gamma solve are skipped by frozen problems
 };
 
 // ---- host-side launch helpers (defined in the .cu files) -------------------------------
@@ -109,7 +123,7 @@ struct LaunchCfg {
 // NLM over the items: reads slot sa.src (or sa.src_ptr), writes f_override or each
 // problem's f buffer.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_is_bf16, cudaStream_t s,
+                       StepArgs sa, int src_type, cudaStream_t s,
                        float *f_override = nullptr, int occ = 4);
 // FFT launches: items carry (prob, first row/col, count). tw_cap = largest transform
 // length in the launch (M for rows, H for columns); buf_cap = largest per-item buffer
@@ -189,16 +203,32 @@ __host__ __device__ __forceinline__ int mirror_index(int i, int n) {
   return i < n ? i : p - 1 - i;
 }
 
-__device__ __forceinline__ float load_img(const void *base, long idx, int is_bf16) {
-  if (is_bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
+// Storage types of the iterate ring (ProbDev::storage): kStoreF32, kStoreBF16, kStoreF16.
+// Arithmetic is FP32 in every case; a 16-bit type only changes how iterates are kept.
+enum StoreType { kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2 };
+
+__host__ __device__ __forceinline__ int store_bytes(int type) { return type ? 2 : 4; }
+
+__device__ __forceinline__ float load_img(const void *base, long idx, int type) {
+  if (type == kStoreBF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
+  if (type == kStoreF16) return __half2float(reinterpret_cast<const __half *>(base)[idx]);
   return reinterpret_cast<const float *>(base)[idx];
 }
 
-__device__ __forceinline__ void store_img(void *base, long idx, float v, int is_bf16) {
-  if (is_bf16)
+__device__ __forceinline__ void store_img(void *base, long idx, float v, int type) {
+  if (type == kStoreBF16)
     reinterpret_cast<__nv_bfloat16 *>(base)[idx] = __float2bfloat16_rn(v);
+  else if (type == kStoreF16)
+    reinterpret_cast<__half *>(base)[idx] = __float2half_rn(v);
   else
     reinterpret_cast<float *>(base)[idx] = v;
+}
+
+// The value a store of v in `type` keeps (round to nearest even).
+__device__ __forceinline__ float round_to_storage(float v, int type) {
+  if (type == kStoreBF16) return __bfloat162float(__float2bfloat16_rn(v));
+  if (type == kStoreF16) return __half2float(__float2half_rn(v));
+  return v;
 }
 
 }  // namespace red

@@ -302,18 +302,18 @@ struct StepOut {
   StepArgs sa;
   void *dst_ring;
   const void *src_ring;
-  int src_bf16;
+  int src_type;
   __device__ __forceinline__ void init(const ProbDev *p, const StepArgs &s) {
     P = p;
     sa = s;
-    const int esz = P->storage ? 2 : 4;
+    const int esz = store_bytes(P->storage);
     dst_ring = static_cast<char *>(P->ring) + (size_t)sa.dst * P->slot_stride * esz;
     src_ring = sa.src_ptr ? sa.src_ptr
                           : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
-    src_bf16 = sa.src_ptr ? 0 : P->storage;
+    src_type = sa.src_ptr ? kStoreF32 : P->storage;
   }
   __device__ __forceinline__ float2 prev(long base) const {
-    return make_float2(load_img(src_ring, base, src_bf16), load_img(src_ring, base + 1, src_bf16));
+    return make_float2(load_img(src_ring, base, src_type), load_img(src_ring, base + 1, src_type));
   }
   // writes x_{k+1}[base], [base+1] = (xe, xo); accumulates the statistics against pv
   __device__ __forceinline__ void put(long base, float xe, float xo, float2 pv, float &sd,
@@ -324,10 +324,8 @@ struct StepOut {
     } else {
       store_img(dst_ring, base, xe, P->storage);
       store_img(dst_ring, base + 1, xo, P->storage);
-      if (P->storage) {
-        ye = __bfloat162float(__float2bfloat16_rn(xe));
-        yo = __bfloat162float(__float2bfloat16_rn(xo));
-      }
+      ye = round_to_storage(xe, P->storage);
+      yo = round_to_storage(xo, P->storage);
     }
     sd = fmaf(ye - pv.x, ye - pv.x, sd);
     sd = fmaf(yo - pv.y, yo - pv.y, sd);

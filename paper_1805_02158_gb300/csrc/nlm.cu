@@ -51,7 +51,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int R, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_items, StepArgs sa,
-      int src_is_bf16_override, float *f_override) {
+      int src_type_override, float *f_override) {
   extern __shared__ float smem_tiles[];
   // one independent tile of 60 x R outputs per warp (work units are warp-sized so they
   // spread evenly over the SMs); the warp stages its own tile + 7-pixel halo
@@ -68,14 +68,14 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
   const float k = P->nlm_k;
 
   const void *src;
-  int bf16;
+  int stype;
   if (sa.src_ptr) {
     src = sa.src_ptr;
-    bf16 = src_is_bf16_override;
+    stype = src_type_override;
   } else {
-    bf16 = P->storage;
+    stype = P->storage;
     src = static_cast<const char *>(P->ring) +
-          (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
+          (size_t)sa.src * P->slot_stride * store_bytes(stype);
   }
 
   // Stage the tile: kStageU loads in flight per lane. One reflection is exact for every
@@ -93,7 +93,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
         const int cc = idx - rr * kCols;
         const int gr = reflect_clamp(tr0 - 7 + rr, H);
         const int gc = reflect_clamp(tc0 - 7 + cc, W);
-        v[u] = load_img(src, (long)gr * W + gc, bf16);
+        v[u] = load_img(src, (long)gr * W + gc, stype);
       }
     }
 #pragma unroll
@@ -223,7 +223,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
 template <int R, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_items, StepArgs sa,
-         int src_is_bf16_override, float *f_override) {
+         int src_type_override, float *f_override) {
   extern __shared__ float smem_tiles[];
   const int item = blockIdx.x * blockDim.y + threadIdx.y;
   if (item >= n_items) return;
@@ -238,14 +238,14 @@ k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int 
   const float k = P->nlm_k;
 
   const void *src;
-  int bf16;
+  int stype;
   if (sa.src_ptr) {
     src = sa.src_ptr;
-    bf16 = src_is_bf16_override;
+    stype = src_type_override;
   } else {
-    bf16 = P->storage;
+    stype = P->storage;
     src = static_cast<const char *>(P->ring) +
-          (size_t)sa.src * P->slot_stride * (bf16 ? 2 : 4);
+          (size_t)sa.src * P->slot_stride * store_bytes(stype);
   }
 
   // staging: as in k_nlm
@@ -261,7 +261,7 @@ k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int 
         const int cc = idx - rr * kCols;
         const int gr = reflect_clamp(tr0 - 7 + rr, H);
         const int gc = reflect_clamp(tc0 - 7 + cc, W);
-        v[u] = load_img(src, (long)gr * W + gc, bf16);
+        v[u] = load_img(src, (long)gr * W + gc, stype);
       }
     }
 #pragma unroll
@@ -358,7 +358,7 @@ cudaError_t nlm_prepare(int wy) {
 // occ: 3 or 4 resident CTAs per SM (the register budget: 161 or 128 per thread); the
 // arithmetic, and so the result, is the same for both.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_is_bf16, cudaStream_t s, float *f_override, int occ) {
+                       StepArgs sa, int src_type, cudaStream_t s, float *f_override, int occ) {
   if (n_items <= 0) return cudaSuccess;
   if (wy < 1 || wy > 4) return cudaErrorInvalidValue;   // kernel is bounded at 128 threads
   const size_t smem = (size_t)wy * (kNlmR + 14) * kStride * sizeof(float);
@@ -366,13 +366,13 @@ cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items,
   const int ctas = (n_items + wy - 1) / wy;
   if (nlm_packed()) {
     if (occ >= 4)
-      k_nlm_x2<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
+      k_nlm_x2<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
     else
-      k_nlm_x2<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
+      k_nlm_x2<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
   } else if (occ >= 4) {
-    k_nlm<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
+    k_nlm<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
   } else {
-    k_nlm<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_is_bf16, f_override);
+    k_nlm<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
   }
   count_launches(1);
   return cudaGetLastError();

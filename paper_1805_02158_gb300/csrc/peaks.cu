@@ -1,6 +1,6 @@
-// Throughput microbenchmarks of the arithmetic units the hot path is bound by: FP32 FMA
-// (the NLM's distance and accumulation arithmetic), the EX2 special-function unit (its
-// weights) and FP64 FMA (the extrapolation solve). Each thread runs independent
+// Throughput microbenchmarks of the arithmetic units the hot path is bound by: FP32 FMA,
+// scalar and packed f32x2 (the NLM's distance and accumulation arithmetic), the EX2
+// special-function unit (its weights) and FP64 FMA (the extrapolation solve). Each thread runs independent
 // dependency chains long enough that issue, not latency, limits them (the iteration loop
 // is unrolled so that loop overhead is a few percent of the issue slots); the grid fills
 // every SM. Used by the benchmark to put the derived peaks beside measured ones.
@@ -29,6 +29,34 @@ __global__ void __launch_bounds__(256) k_fp32_fma(float *out, float seed) {
 #pragma unroll
   for (int c = 0; c < kChains; ++c) s += a[c];
   if (s == 12345.f) out[threadIdx.x] = s;   // keeps the chains alive
+}
+
+// Packed FP32 (fma.rn.f32x2, sm_100 and later): each instruction does two lane FMAs on a
+// 64-bit register pair; counted as two lane operations.
+__global__ void __launch_bounds__(256) k_fp32x2_fma(float *out, float seed) {
+  unsigned long long a[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    const float lo = seed + threadIdx.x * 1e-7f + c, hi = lo + 0.5f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a[c]) : "f"(lo), "f"(hi));
+  }
+  unsigned long long m, b;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(m) : "f"(0.999999f), "f"(0.999998f));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(1e-7f), "f"(2e-7f));
+#pragma unroll 8
+  for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+      asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[c]) : "l"(m), "l"(b));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[c]));
+    s += lo + hi;
+  }
+  if (s == 12345.f) out[threadIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(256) k_ex2(float *out, float seed) {
@@ -90,9 +118,11 @@ double time_launch(Launch &&launch, cudaStream_t s) {
 using namespace red;
 
 extern "C" red_status red_measure_peaks(double *fp32_fma_lane_ops, double *ex2_lane_ops,
-                                        double *fp64_fma_lane_ops, void *stream) {
+                                        double *fp64_fma_lane_ops,
+                                        double *fp32x2_fma_lane_ops, void *stream) {
   return guarded([&] {
-    CHECK_ARG(fp32_fma_lane_ops && ex2_lane_ops && fp64_fma_lane_ops, "null argument");
+    CHECK_ARG(fp32_fma_lane_ops && ex2_lane_ops && fp64_fma_lane_ops && fp32x2_fma_lane_ops,
+              "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0, sms = 0;
     CUDA_OK(cudaGetDevice(&dev));
@@ -103,11 +133,13 @@ extern "C" red_status red_measure_peaks(double *fp32_fma_lane_ops, double *ex2_l
     const double lanes = (double)blocks * threads * kChains;
     double ms = time_launch([&] { k_fp32_fma<<<blocks, threads, 0, s>>>((float *)buf, 1.f); }, s);
     *fp32_fma_lane_ops = lanes * kIters / (ms * 1e-3);
+    ms = time_launch([&] { k_fp32x2_fma<<<blocks, threads, 0, s>>>((float *)buf, 1.f); }, s);
+    *fp32x2_fma_lane_ops = 2.0 * lanes * kIters / (ms * 1e-3);
     ms = time_launch([&] { k_ex2<<<blocks, threads, 0, s>>>((float *)buf, 1.f); }, s);
     *ex2_lane_ops = lanes * kIters / (ms * 1e-3);
     ms = time_launch([&] { k_fp64_fma<<<blocks, threads, 0, s>>>((double *)buf, 1.0); }, s);
     *fp64_fma_lane_ops = lanes * (kIters / 16) / (ms * 1e-3);
-    count_launches(18);
+    count_launches(24);
     CUDA_OK(cudaFree(buf));
     return RED_OK;
   });

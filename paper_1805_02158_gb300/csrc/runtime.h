@@ -86,7 +86,7 @@ struct CycleOp {
   int out;
 };
 
-void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_bf16,
+void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_type,
                     cudaStream_t s);
 void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs &va,
                cudaStream_t s);

@@ -66,17 +66,17 @@ struct Request {
 
 std::string key_of(const red_config &c, const std::vector<float> &psf) {
   std::ostringstream o;
-  o << std::setprecision(17);   // sigma, alpha and h round-trip: equal keys, equal physics
+  // sigma, alpha and h printed so that they round-trip, and every PSF tap by its raw bits:
+  // equal keys mean equal physics (no hash, so no collisions)
+  o << std::setprecision(17);
   o << c.task << "|" << c.height << "x" << c.width << "|" << c.scale << "|" << c.psf_h << "x"
     << c.psf_w << "|" << c.sigma << "|" << c.alpha << "|" << c.nlm_h << "|" << c.ve << "|"
-    << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|";
-  uint64_t h = 1469598103934665603ull;
+    << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|" << std::hex;
   for (float v : psf) {
     uint32_t u;
     std::memcpy(&u, &v, 4);
-    h = (h ^ u) * 1099511628211ull;
+    o << std::setw(8) << std::setfill('0') << u;
   }
-  o << h;
   return o.str();
 }
 
@@ -214,7 +214,7 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   if (P->pd.storage == 0) {
     CUDA_OK(cudaMemcpyAsync(blk + P->L.ring, x0p, (size_t)H * W * 4, cudaMemcpyHostToDevice, s));
   } else {
-    // bf16 history: stage through f32 and convert with the copy kernel
+    // 16-bit history (bf16 or f16): stage through f32 and convert with the copy kernel
     CUDA_OK(cudaMemcpyAsync(blk + P->L.tmp, x0p, (size_t)H * W * 4, cudaMemcpyHostToDevice, s));
     CUDA_OK(launch_convert_to_slot(P->d_pd, reinterpret_cast<float *>(blk + P->L.tmp), 0, s));
   }

@@ -422,10 +422,10 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
     aps = P->cg_ap + e0;
   }
   const float *f = P->f, *b0 = P->b0;
-  const int esz = P->storage ? 2 : 4;
+  const int esz = store_bytes(P->storage);
   const void *xin = sa.src_ptr ? sa.src_ptr
                                : static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * esz;
-  const int in_bf16 = sa.src_ptr ? 0 : P->storage;
+  const int in_type = sa.src_ptr ? kStoreF32 : P->storage;
   constexpr int kU = 4;   // elements per thread per batch of independent loads
 
   // x = x_k (warm start) into the band and global memory (S B x reads the halo rows)
@@ -434,7 +434,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int l = l0 + u * kSrThreads;
-      if (l < nl) v[u] = load_img(xin, e0 + l, in_bf16);
+      if (l < nl) v[u] = load_img(xin, e0 + l, in_type);
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -578,7 +578,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       const int l = l0 + u * kSrThreads;
       if (l < nl) {
         xv[u] = xs[l];
-        xo[u] = load_img(xin, e0 + l, in_bf16);
+        xo[u] = load_img(xin, e0 + l, in_type);
       }
     }
 #pragma unroll
@@ -590,7 +590,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
           sa.dst_ptr[e0 + l] = v;
         } else {
           store_img(dst_ring, e0 + l, v, P->storage);
-          if (P->storage) v = __bfloat162float(__float2bfloat16_rn(v));
+          v = round_to_storage(v, P->storage);
         }
         sd = fmaf(v - xo[u], v - xo[u], sd);
         sx = fmaf(xo[u], xo[u], sx);

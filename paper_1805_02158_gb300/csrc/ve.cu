@@ -44,8 +44,9 @@ __device__ __forceinline__ const float *vec_ptr(const ProbDev *P, const VeArgs &
   return static_cast<const float *>(P->ring) + (size_t)va.slots[i] * P->slot_stride;
 }
 
-__device__ __forceinline__ const __nv_bfloat16 *vec_ptr_bf16(const ProbDev *P, const VeArgs &va, int i) {
-  return static_cast<const __nv_bfloat16 *>(P->ring) + (size_t)va.slots[i] * P->slot_stride;
+// A 16-bit ring slot (BF16 or FP16 storage).
+__device__ __forceinline__ const void *vec_ptr_16(const ProbDev *P, const VeArgs &va, int i) {
+  return static_cast<const char *>(P->ring) + (size_t)va.slots[i] * P->slot_stride * 2;
 }
 
 template <int K>
@@ -96,8 +97,8 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
   GramAcc<K> acc;
   acc.zero();
   const int tid = threadIdx.x;
-  const bool bf16 = (va.ptrs[0] == nullptr) && P->storage;
-  if (!bf16) {
+  const int stype = (va.ptrs[0] == nullptr) ? P->storage : kStoreF32;
+  if (stype == kStoreF32) {
     const float *xp[K + 1];
 #pragma unroll
     for (int i = 0; i <= K; ++i) xp[i] = vec_ptr(P, va, i);
@@ -155,13 +156,13 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
       acc.add(x);
     }
   } else {
-    const __nv_bfloat16 *xp[K + 1];
+    const void *xp[K + 1];
 #pragma unroll
-    for (int i = 0; i <= K; ++i) xp[i] = vec_ptr_bf16(P, va, i);
+    for (int i = 0; i <= K; ++i) xp[i] = vec_ptr_16(P, va, i);
     for (int p = begin + tid; p < end; p += blockDim.x) {
       float x[K + 1];
 #pragma unroll
-      for (int i = 0; i <= K; ++i) x[i] = __bfloat162float(xp[i][p]);
+      for (int i = 0; i <= K; ++i) x[i] = load_img(xp[i], p, stype);
       acc.add(x);
     }
   }
@@ -472,8 +473,8 @@ k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeA
 #pragma unroll
   for (int j = 0; j < kap; ++j) xi[j] = (float)P->ve_coef[j];
   const bool explicit_io = va.ptrs[0] != nullptr;
-  const int bf16 = explicit_io ? 0 : P->storage;
-  const int esz = bf16 ? 2 : 4;
+  const int stype = explicit_io ? kStoreF32 : P->storage;
+  const int esz = store_bytes(stype);
   void *out = va.out_ptr ? (void *)va.out_ptr
                          : static_cast<char *>(P->ring) + (size_t)va.out_slot * P->slot_stride * esz;
   const void *xs[K + 1];
@@ -481,7 +482,7 @@ k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeA
   for (int i = 0; i <= K; ++i)
     xs[i] = va.ptrs[i] ? (const void *)va.ptrs[i]
                        : static_cast<const char *>(P->ring) + (size_t)va.slots[i] * P->slot_stride * esz;
-  bool vec = !bf16 && ((begin & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  bool vec = stype == kStoreF32 && ((begin & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
 #pragma unroll
   for (int i = 0; i <= K; ++i) vec = vec && ((reinterpret_cast<uintptr_t>(xs[i]) & 15) == 0);
   int p0 = begin;
@@ -513,20 +514,20 @@ k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeA
   for (int p = p0 + threadIdx.x; p < end; p += blockDim.x) {
     float val;
     if (brk) {
-      val = load_img(xs[K], p, bf16);
+      val = load_img(xs[K], p, stype);
     } else {
-      float prev = load_img(xs[0], p, bf16);
+      float prev = load_img(xs[0], p, stype);
       const float x0 = prev;
       float acc = 0.f;
 #pragma unroll
       for (int j = 0; j < kap; ++j) {
-        const float nx = load_img(xs[j + 1], p, bf16);
+        const float nx = load_img(xs[j + 1], p, stype);
         acc = fmaf(xi[j], nx - prev, acc);
         prev = nx;
       }
       val = x0 + acc;
     }
-    store_img(out, p, val, bf16);
+    store_img(out, p, val, stype);
   }
 }
 
@@ -538,7 +539,7 @@ k_copy_slots(const ProbDev *__restrict__ probs, const Item *__restrict__ items, 
   const ProbDev *P = probs + it.prob;
   const int begin = it.a * kGramChunk;
   const int end = min(P->N, begin + kGramChunk);
-  const int esz = P->storage ? 2 : 4;
+  const int esz = store_bytes(P->storage);
   float *user = ptrs[it.prob];
   if (mode == 0) {
     void *dst = static_cast<char *>(P->ring) + (size_t)slot * P->slot_stride * esz;
@@ -551,7 +552,7 @@ k_copy_slots(const ProbDev *__restrict__ probs, const Item *__restrict__ items, 
 
 // One problem's ring slot <-> a float32 image (storage conversion included).
 __global__ void k_slot_io(const ProbDev *__restrict__ P, int slot, float *img, int to_slot) {
-  const int esz = P->storage ? 2 : 4;
+  const int esz = store_bytes(P->storage);
   char *ring = static_cast<char *>(P->ring) + (size_t)slot * P->slot_stride * esz;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P->N; e += (long)gridDim.x * blockDim.x) {
     if (to_slot)
@@ -563,14 +564,25 @@ __global__ void k_slot_io(const ProbDev *__restrict__ P, int slot, float *img, i
 
 }  // namespace
 
+// SMs of the current device (grid size of the grid-stride slot copies).
+static int current_device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
 cudaError_t launch_convert_to_slot(const ProbDev *d_prob, const float *src, int slot, cudaStream_t s) {
-  k_slot_io<<<152, 256, 0, s>>>(d_prob, slot, const_cast<float *>(src), 1);
+  k_slot_io<<<current_device_sms(), 256, 0, s>>>(d_prob, slot, const_cast<float *>(src), 1);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fetch_slot(const ProbDev *d_prob, int slot, float *dst, cudaStream_t s) {
-  k_slot_io<<<152, 256, 0, s>>>(d_prob, slot, dst, 0);
+  k_slot_io<<<current_device_sms(), 256, 0, s>>>(d_prob, slot, dst, 0);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -796,20 +808,31 @@ __global__ void __launch_bounds__(256) k_combine_static(StaticVe a) {
   }
 }
 
-// Device address of g_ve_scratch, looked up once per device with that device current.
+// Device address of g_ve_scratch and the device's SM count, looked up once per device
+// with that device current.
 std::mutex g_static_mu;
 std::vector<double *> g_static_addr;
+std::vector<int> g_static_sms;
 
-double *static_scratch(int dev) {
+double *static_scratch(int dev, int *sms) {
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+  if ((int)g_static_addr.size() <= dev) {
+    g_static_addr.resize(dev + 1, nullptr);
+    g_static_sms.resize(dev + 1, 0);
+  }
   if (!g_static_addr[dev]) {
     void *ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ve_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_ve_scratch);
     if (e != cudaSuccess)
       throw Fail{RED_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n < 1)
+      throw Fail{RED_ECUDA, std::string("cudaDeviceGetAttribute(SM count): ") + cudaGetErrorString(e)};
+    g_static_sms[dev] = n;
     g_static_addr[dev] = static_cast<double *>(ptr);
   }
+  *sms = g_static_sms[dev];
   return g_static_addr[dev];
 }
 
@@ -833,7 +856,8 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
                                  std::to_string(max_n) + " elements per vector"};
     int dev = 0;
     CUDA_OK(cudaGetDevice(&dev));
-    double *scratch = static_scratch(dev);
+    int sms = 0;
+    double *scratch = static_scratch(dev, &sms);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     StaticVe a{};
     for (int i = 0; i < n_vec; ++i) {
@@ -852,7 +876,8 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
     // the state block starts at zero; every partial, xi and gamma read is written first
     CUDA_OK(cudaMemsetAsync(a.st, 0, sizeof(ProbState), s));
     const int K = n_vec - 1;
-    const int comb_ctas = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 4 * 152);
+    // grid-stride combine: at most 4 resident 256-thread CTAs per SM of this device
+    const int comb_ctas = (int)std::min<int64_t>((n / 4 + 255) / 256 + 1, 4 * (int64_t)sms);
     switch (K) {
 #define RED_STATIC_CASE(k)                                      \
   case k:                                                       \

@@ -29,6 +29,8 @@ F32, BF16, F16 = 0, 1, 2
 PHASE_NLM, PHASE_FFT, PHASE_CG, PHASE_GRAM, PHASE_VESOLVE, PHASE_COMBINE = range(6)
 VE_NAMES = {"none": VE_NONE, "mpe": VE_MPE, "rre": VE_RRE, "svdmpe": VE_SVDMPE}
 STORAGE_NAMES = {"f32": F32, "bf16": BF16, "f16": F16}
+BASE_FP, BASE_SD = 0, 1
+BASELINE_NAMES = {"fp": BASE_FP, "sd": BASE_SD}
 
 
 class Config(ctypes.Structure):
@@ -40,6 +42,7 @@ class Config(ctypes.Structure):
         ("nlm_patch", ctypes.c_int), ("nlm_search", ctypes.c_int), ("nlm_h", ctypes.c_double),
         ("ve", ctypes.c_int), ("ve_k", ctypes.c_int), ("ve_m", ctypes.c_int),
         ("cg_iters", ctypes.c_int), ("storage", ctypes.c_int),
+        ("baseline", ctypes.c_int), ("sd_mu", ctypes.c_double), ("ve_freeze", ctypes.c_int),
     ]
 
 
@@ -104,7 +107,8 @@ _SIGS = {
     "red_problem_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
     "red_kernel_launches": (ctypes.c_uint64, []),
     "red_measure_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p]),
 }
 
 
@@ -125,11 +129,12 @@ def lib():
 
 
 def measure_peaks(stream=None):
-    """Measured FP32-FMA, EX2 and FP64-FMA throughputs (lane operations / s, whole device)."""
-    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    """Measured FP32-FMA, EX2, FP64-FMA and packed f32x2-FMA throughputs (lane operations / s,
+    whole device)."""
+    a, b, c, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().red_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                   _stream_ptr(stream)), "red_measure_peaks")
-    return {"fp32_fma": a.value, "ex2": b.value, "fp64_fma": c.value}
+                                   ctypes.byref(d), _stream_ptr(stream)), "red_measure_peaks")
+    return {"fp32_fma": a.value, "ex2": b.value, "fp64_fma": c.value, "fp32x2_fma": d.value}
 
 
 def status_string(st: int) -> str:
@@ -170,7 +175,7 @@ def _dptr(t, shape=None):
 
 def make_config(task="deblur", height=64, width=64, scale=1, psf=None, sigma=2 ** 0.5,
                 alpha=0.02, nlm_h=10.0, ve="rre", ve_k=5, ve_m=0, cg_iters=20,
-                storage="f32"):
+                storage="f32", baseline="fp", sd_mu=0.0, ve_freeze=0):
     """Builds a red_config; `psf` is a 2-D float array (kept referenced by the config)."""
     import numpy as np
     c = Config()
@@ -184,6 +189,8 @@ def make_config(task="deblur", height=64, width=64, scale=1, psf=None, sigma=2 *
     c.ve = VE_NAMES[ve] if isinstance(ve, str) else int(ve)
     c.ve_k, c.ve_m, c.cg_iters = int(ve_k), int(ve_m), int(cg_iters)
     c.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+    c.baseline = BASELINE_NAMES[baseline] if isinstance(baseline, str) else int(baseline)
+    c.sd_mu, c.ve_freeze = float(sd_mu), int(ve_freeze)
     c._psf_keepalive = psf
     return c
 
