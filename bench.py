@@ -311,27 +311,45 @@ def cufft_comparison(problems, torch, steps=200, reps=5):
 STUDY_VARIANTS = (("rre", 5), ("mpe", 5), ("rre", 10), ("mpe", 10))
 
 
+def _residual_trace(B, x0s, outs, n):
+    """Fixed-point residual ||F(x) - x|| / ||x|| against denoiser calls (budgets 5, 10, ..,
+    CALLS): the relative change of a solve's last FP step is the residual at the point that
+    step started from. Per budget, one value per image."""
+    trace = []
+    for calls in range(5, CALLS + 1, 5):
+        st = B.solve(x0s, outs, calls, 0.0)
+        trace.append([s["rel_change"] for s in st[:n]])
+    return trace
+
+
 def _fp_reference(problems, ys, x0s, outs, red):
-    """Plain FP (no extrapolation) after CALLS denoiser calls: per-image PSNR and objective."""
+    """Plain FP (no extrapolation) after CALLS denoiser calls: per-image PSNR, objective and
+    the residual trace."""
     fpP = [red.Problem(red.config_for(p, ve="none"), y) for p, y in zip(problems, ys)]
     B = red.Batch(fpP)
+    trace = _residual_trace(B, x0s, outs, len(problems))
     B.solve(x0s, outs, CALLS, 0.0)
     xfp = [o.cpu().numpy().astype(np.float64) for o in outs]
     psnr_fp = [10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2)) for x, p in zip(xfp, problems)]
     e_fp = [P.objective(o) for P, o in zip(fpP, outs)]
-    return psnr_fp, e_fp
+    return psnr_fp, e_fp, trace
 
 
-def _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp, final_objective=False):
-    """Denoiser calls the solves of VP need to reach plain FP's PSNR and objective, probing
+def _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp, final_objective=False,
+                    res_fp=None):
+    """Denoiser calls the solves of VP need to reach plain FP's PSNR, objective and (with
+    res_fp, plain FP's residual after CALLS calls per image) fixed-point residual, probing
     budgets in steps of 5 calls up to CALLS (None: not reached); optionally the objective
-    after CALLS calls as a fraction of plain FP's."""
+    after CALLS calls as a fraction of plain FP's; and the residual trace."""
     n = len(problems)
     Bv = red.Batch(VP)
     need_psnr = [None] * n
     need_cost = [None] * n
+    need_res = [None] * n
+    trace = []
     for calls in range(5, CALLS + 1, 5):
-        Bv.solve(x0s, outs, calls, 0.0)
+        st = Bv.solve(x0s, outs, calls, 0.0)
+        trace.append([s["rel_change"] for s in st])
         for i, (o, p, P) in enumerate(zip(outs, problems, VP)):
             x = o.cpu().numpy().astype(np.float64)
             ps = 10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
@@ -339,13 +357,18 @@ def _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp, final_objective
                 need_psnr[i] = calls
             if need_cost[i] is None and P.objective(o) <= e_fp[i]:
                 need_cost[i] = calls
-        if all(v is not None for v in need_psnr + need_cost):
-            break
+            if res_fp is not None and need_res[i] is None and st[i]["rel_change"] <= res_fp[i]:
+                need_res[i] = calls
     ratio = None
     if final_objective:
         Bv.solve(x0s, outs, CALLS, 0.0)
         ratio = [P.objective(o) / e for P, o, e in zip(VP, outs, e_fp)]
-    return need_cost, need_psnr, ratio
+    return need_cost, need_psnr, ratio, need_res, trace
+
+
+def _every(trace, k=4):
+    """Every k-th budget of a residual trace (5, 25, 45, ... calls), mean over the images."""
+    return [float(np.mean(t)) for t in trace[::k]]
 
 
 def _mean_reached(v):
@@ -361,22 +384,32 @@ def ve_vs_fp_study(problems, Ps, torch, red, variants_to_run=STUDY_VARIANTS):
     ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
     x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in problems]
     outs = [torch.empty_like(x) for x in x0s]
-    psnr_fp, e_fp = _fp_reference(problems, ys, x0s, outs, red)
+    psnr_fp, e_fp, res_trace_fp = _fp_reference(problems, ys, x0s, outs, red)
+    res_fp = res_trace_fp[-1]
     variants = {}
     for method, k in variants_to_run:
         VP = Ps if (Ps is not None and (method, k) == ("rre", VE_K)) else \
             [red.Problem(red.config_for(p, ve=method, ve_k=k), y) for p, y in zip(problems, ys)]
-        need_cost, need_psnr, _ = _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp)
+        need_cost, need_psnr, _, need_res, trace = _calls_to_reach(
+            red, VP, problems, x0s, outs, psnr_fp, e_fp, res_fp=res_fp)
         variants[f"{method}_k{k}"] = {
             "calls_to_fp200_cost": need_cost, "calls_to_fp200_psnr": need_psnr,
+            "calls_to_fp200_residual": need_res,
             "cost_reached": sum(c is not None for c in need_cost),
             "psnr_reached": sum(c is not None for c in need_psnr),
+            "residual_reached": sum(c is not None for c in need_res),
             "cost_calls_mean_reached": _mean_reached(need_cost),
-            "psnr_calls_mean_reached": _mean_reached(need_psnr)}
+            "psnr_calls_mean_reached": _mean_reached(need_psnr),
+            "residual_calls_mean_reached": _mean_reached(need_res),
+            "residual_every20_calls_mean": _every(trace)}
     main = variants.get(f"rre_k{VE_K}", {})
     return {"fp_calls": CALLS, "fp200_psnr_db_mean": float(np.mean(psnr_fp)),
+            "fp200_residual_mean": float(np.mean(res_fp)),
+            "fp_residual_every20_calls_mean": _every(res_trace_fp),
+            "residual": "||F(x) - x|| / ||x|| at the input of the last FP step (rel_change)",
             "rre_calls_to_fp200_cost_mean": main.get("cost_calls_mean_reached"),
             "rre_calls_to_fp200_psnr_mean": main.get("psnr_calls_mean_reached"),
+            "rre_calls_to_fp200_residual_mean": main.get("residual_calls_mean_reached"),
             "variants": variants}
 
 
@@ -398,15 +431,15 @@ def mk_sweep_study(torch, red, seeds=(0, 1, 2), methods=SWEEP_METHODS, ms=SWEEP_
     ys = [torch.from_numpy(p.y.astype(np.float32)).cuda() for p in problems]
     x0s = [torch.from_numpy(p.x0.astype(np.float32)).cuda() for p in problems]
     outs = [torch.empty_like(x) for x in x0s]
-    psnr_fp, e_fp = _fp_reference(problems, ys, x0s, outs, red)
+    psnr_fp, e_fp, _ = _fp_reference(problems, ys, x0s, outs, red)
     grid, best = {}, {}
     for method in methods:
         for m in ms:
             for kappa in kappas:
                 VP = [red.Problem(red.config_for(p, ve=method, ve_k=kappa + 1, ve_m=m), y)
                       for p, y in zip(problems, ys)]
-                need_cost, _, ratio = _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp, e_fp,
-                                                      final_objective=True)
+                need_cost, _, ratio, _, _ = _calls_to_reach(red, VP, problems, x0s, outs, psnr_fp,
+                                                            e_fp, final_objective=True)
                 row = {"calls_to_fp200_cost": need_cost,
                        "cost_reached": sum(c is not None for c in need_cost),
                        "cost_calls_mean_reached": _mean_reached(need_cost),
@@ -489,7 +522,7 @@ def serving_leg(red, n_req, budget_gb=32, slots=32):
     """Poisson arrivals (200 req/s) of mixed deblurring / x3 SR requests, sides 128-1024,
     rel-change tolerance 1e-4, cap 300 FP calls, through the serving loop; latency is
     submission to completion (host result written). RRE k = 5, then plain FP on the same
-    stream for comparison."""
+    stream for comparison; each broken down by task and by image side."""
     import multiprocessing as mp
     from paper_1805_02158_gb300 import synth
     ctx = mp.get_context("spawn")
@@ -528,16 +561,32 @@ def serving_leg(red, n_req, budget_gb=32, slots=32):
         if not good:
             out["rre" if ve == "rre" else "plain_fp"] = {"failed": failed}
             continue
+        tasks = [reqs[i]["task"] for i in good]
+        sides = [max(reqs[i]["height"], reqs[i]["width"]) for i in good]
         stats = [stats[i] for i in good]
         lat = np.array([s["ms_total"] for s in stats])
         calls = np.array([s["fp_calls"] for s in stats])
+        conv = np.array([s["converged"] for s in stats], dtype=np.float64)
         pix = np.array([reqs[i]["height"] * reqs[i]["width"] for i in good])
+
+        def summary(sel):
+            sel = np.asarray(sel, dtype=bool)
+            if not sel.any():
+                return None
+            return {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                    "p99_ms": float(np.percentile(lat[sel], 99)),
+                    "fp_calls_mean": float(calls[sel].mean()),
+                    "converged_frac": float(conv[sel].mean())}
+
         out["rre" if ve == "rre" else "plain_fp"] = {
             "failed": failed,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "solves_per_s": n_req / wall, "mpix_iter_per_s": float((pix * calls).sum()) / wall / 1e6,
             "fp_calls_mean": float(calls.mean()),
-            "converged_frac": float(np.mean([s["converged"] for s in stats])), "wall_s": wall}
+            "converged_frac": float(conv.mean()), "wall_s": wall,
+            "by_task": {t: summary([x == t for x in tasks]) for t in ("deblur", "sr")},
+            "by_side": {f"<={lim}": summary([lo < sd <= lim for sd in sides])
+                        for lo, lim in ((0, 256), (256, 512), (512, 1024))}}
     return out
 
 
@@ -551,7 +600,7 @@ def main():
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer (0: none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the serving leg (0: skip it)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the SR and uneven-batch workloads")

@@ -128,8 +128,10 @@ red_status red_set_observation(red_problem p, const void *y, int y_is_host, void
 
 red_status red_destroy_problem(red_problem p);
 
-/* One FP step, Eq. (7): x_out = [H^T H/sigma^2 + alpha I]^{-1}[H^T y/sigma^2 + alpha f(x_in)].
- * x_in_dev, x_out_dev: device float32 images (distinct buffers). */
+/* One FP step, Eq. (7): x_out = [H^T H/sigma^2 + alpha I]^{-1}[H^T y/sigma^2 + alpha f(x_in)]
+ * (or, with baseline RED_BASE_SD, the steepest-descent step x_in - mu grad E(x_in) of Eq. (5)).
+ * x_in_dev, x_out_dev: device float32 images, distinct, 8-byte aligned (RED_EINVAL
+ * otherwise). */
 red_status red_fp_step(red_problem p, const void *x_in_dev, void *x_out_dev, void *stream);
 
 /* The denoiser alone: f_dev = f(x_dev), pixelwise non-local means (the role of f in
@@ -179,8 +181,8 @@ red_status red_ve_extrapolate_static(const void *const *xs_dev, int n_vec, int64
 red_status red_solve(red_problem p, const void *x0_dev, int max_fp_calls, double rel_tol,
                      void *x_out_dev, red_stats *stats, void *stream);
 
-/* Evaluates the objective E(x) of Eq. (4) at a device float32 image (one denoiser call);
- * synchronises the stream. */
+/* Evaluates the objective E(x) of Eq. (4) at a device float32 image, 8-byte aligned (one
+ * denoiser call); synchronises the stream. */
 red_status red_objective(red_problem p, const void *x_dev, double *e_host, void *stream);
 
 /* ----------------------------------------------------------------------------------- */

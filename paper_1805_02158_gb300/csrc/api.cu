@@ -101,6 +101,7 @@ static Layout layout_for(const red_config &c, int nslots, int slot_stride) {
   L.cz = sr ? cv.take(lh * lw * 4) : 0;
   L.psf = cv.take((size_t)c.psf_h * c.psf_w * 4);
   L.obj = cv.take(4 * 8);
+  L.sd = cv.take(sizeof(SdParams));
   L.total = cv.off;
   return L;
 }
@@ -133,10 +134,15 @@ static void validate(const red_config *c) {
     throw Fail{RED_EUNSUPPORTED, "only 5x5 patches and 11x11 search windows are supported"};
   CHECK_ARG(c->storage == RED_F32 || c->storage == RED_BF16 || c->storage == RED_F16,
             "storage must be RED_F32, RED_BF16 or RED_F16");
-  CHECK_ARG(c->baseline == RED_BASE_FP || c->baseline == RED_BASE_SD, "bad baseline");
-  CHECK_ARG(c->sd_mu >= 0.0 && c->ve_freeze >= 0, "sd_mu and ve_freeze must be >= 0");
-  if (c->baseline != RED_BASE_FP || c->ve_freeze != 0)
-    throw Fail{RED_EUNSUPPORTED, "the SD baseline and frozen gamma are not built yet"};
+  CHECK_ARG(c->baseline == RED_BASE_FP || c->baseline == RED_BASE_SD,
+            "baseline must be RED_BASE_FP or RED_BASE_SD");
+  CHECK_ARG(c->sd_mu >= 0.0 && std::isfinite(c->sd_mu), "sd_mu must be finite and >= 0");
+  CHECK_ARG(c->ve_freeze >= 0, "ve_freeze must be >= 0");
+  if (c->ve_freeze > 0) {
+    CHECK_ARG(c->ve != RED_VE_NONE, "ve_freeze needs an extrapolation method");
+    // a frozen cycle runs ve_m + ve_k - 1 baseline steps: at least one
+    CHECK_ARG(c->ve_m + c->ve_k >= 2, "ve_freeze needs ve_m + ve_k >= 2");
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -185,24 +191,24 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStre
   std::vector<int> sr, fused;
   row_tw_cap = row_buf_cap = col_tw_cap = col_buf_cap = 0;
   fused_ncta = lc.fft_cluster;
-  fused_tw_m = fused_tw_h = fused_a = fused_buf = 0;
+  fused_tw_m = fused_tw_h = fused_a = fused_buf = fused_cg = 0;
   const int smem_limit = 220 * 1024;
   n_row_items.assign(pds.size(), 0);
   for (int p = 0; p < (int)pds.size(); ++p) {
     const ProbDev &d = pds[p];
-    for (int r0 = 0; r0 < d.H; r0 += kNlmR)
-      for (int c0 = 0; c0 < d.W; c0 += kNlmTW) nlm.push_back({p, r0, c0, 0});
+    nlm_items(p, d.H, d.W, nlm);
     bool to_cluster = false;
     if (d.task == kDeblur && fused_ncta > 0) {
-      int ac = 0, bc = 0;
-      fft_cluster_caps(d.H, d.W, fused_ncta, &ac, &bc);
+      int ac = 0, bc = 0, cgc = 0;
+      fft_cluster_caps(d.H, d.W, fused_ncta, &ac, &bc, &cgc);
       const int tm = std::max(fused_tw_m, d.M), th = std::max(fused_tw_h, d.H);
       const int aa = std::max(fused_a, ac), bb = std::max(fused_buf, bc);
-      if (fft_cluster_smem(tm, th, aa, bb) <= smem_limit) {
+      if (fft_cluster_smem(tm, th, aa, bb, 0) <= smem_limit) {
         fused_tw_m = tm;
         fused_tw_h = th;
         fused_a = aa;
         fused_buf = bb;
+        fused_cg = std::max(fused_cg, cgc);
         fused.push_back(p);
         to_cluster = true;
       }
@@ -223,6 +229,10 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStre
     }
     for (int c = 0; c < d.n_chunks; ++c) chunks.push_back({p, c, 0, 0});
   }
+  // stage C and G in shared memory only while two CTAs still fit on an SM
+  if (fused_cg && fft_cluster_smem(fused_tw_m, fused_tw_h, fused_a, fused_buf, fused_cg) >
+                      kClusterSmemTwoPerSm)
+    fused_cg = 0;
   n_nlm = (int)nlm.size();
   n_rows = (int)rows.size();
   n_cols = (int)cols.size();
@@ -255,6 +265,7 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStre
       CUDA_OK(cudaMemcpy(dev, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice));
   };
   upload(d_items, items_cap, all);
+
   if (n_sr) upload(d_sr, sr_cap_n, sr);
   sr_cap = SrCaps{};
   if (n_sr) {
@@ -306,7 +317,8 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStre
 void prepare_launch_attrs(const Plan &pl) {
   CUDA_OK(nlm_prepare(pl.lc.nlm_wy));
   if (pl.n_fused)
-    CUDA_OK(fft_cluster_prepare(fft_cluster_smem(pl.fused_tw_m, pl.fused_tw_h, pl.fused_a, pl.fused_buf),
+    CUDA_OK(fft_cluster_prepare(fft_cluster_smem(pl.fused_tw_m, pl.fused_tw_h, pl.fused_a, pl.fused_buf,
+                                                 pl.fused_cg),
                                 pl.fused_ncta));
   if (pl.n_rows) CUDA_OK(fft_prepare(pl.row_tw_cap, pl.row_buf_cap, pl.col_tw_cap, pl.col_buf_cap));
   if (pl.n_sr) CUDA_OK(sr_prepare(pl.lc.sr_cluster, sr_smem_bytes(pl.sr_cap, pl.sr_cap.resident)));
@@ -314,6 +326,7 @@ void prepare_launch_attrs(const Plan &pl) {
 
 void Plan::release() {
   if (d_items) cudaFree(d_items);
+
   if (d_sr) cudaFree(d_sr);
   if (d_fused) cudaFree(d_fused);
   d_items = nullptr;
@@ -327,12 +340,13 @@ void Plan::release() {
 void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaStream_t s) {
   if (pl.n_fused)
     CUDA_OK(launch_fft_solve_cluster(d_probs, pl.d_fused, pl.n_fused, pl.fused_ncta, pl.fused_tw_m,
-                                     pl.fused_tw_h, pl.fused_a, pl.fused_buf, sa, s));
+                                     pl.fused_tw_h, pl.fused_a, pl.fused_buf, pl.fused_cg, sa, s));
   if (pl.n_rows) {
+    const int skip = (sa.update_state ? 1 : 0) | (sa.skip_frozen ? 2 : 0);
     CUDA_OK(launch_fft_r2c(d_probs, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
-                           pl.row_buf_cap, nullptr, nullptr, sa.update_state, s));
+                           pl.row_buf_cap, nullptr, nullptr, skip, s, &sa));
     CUDA_OK(launch_fft_cols(d_probs, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,
-                            pl.col_buf_cap, 1, nullptr, sa.update_state, s));
+                            pl.col_buf_cap, 1, nullptr, skip, s));
     CUDA_OK(launch_fft_c2r(d_probs, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
                            pl.row_buf_cap, sa, s));
   }
@@ -349,21 +363,27 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
 // One extrapolation (Algorithm 1 / RRE) over every problem of a plan.
 void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs &va, cudaStream_t s) {
   CUDA_OK(launch_gram(d_probs, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
-  CUDA_OK(launch_ve_solve(d_probs, n_probs, va.nvec, va.update_state, s));
-  CUDA_OK(launch_combine(d_probs, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
+  CUDA_OK(launch_ve_solve(d_probs, n_probs, va.nvec, va.update_state, s, va.skip_frozen));
+  VeArgs vc = va;
+  vc.skip_frozen = 0;   // frozen problems combine with their stored xi
+  CUDA_OK(launch_combine(d_probs, pl.d_items + pl.off_chunks, pl.n_chunks, vc, s));
 }
 
-// The cycle of Algorithm 3 as a list of operations on ring slots.
-std::vector<CycleOp> cycle_ops(int ve, int k, int m) {
+// The cycle of Algorithm 3 as a list of operations on ring slots. With freeze > 0 (cycling
+// with frozen gamma) the last FP step of the window and the Gram and gamma solve are marked
+// to be skipped by problems whose gamma is frozen: for them the same launches run a cycle
+// of m + k - 1 steps and a combine of x_m .. x_{m+k-1} with the stored xi.
+std::vector<CycleOp> cycle_ops(int ve, int k, int m, int freeze) {
   std::vector<CycleOp> ops;
   if (ve == RED_VE_NONE) {
-    for (int i = 0; i < 10; ++i) ops.push_back({0, i % 2, (i + 1) % 2, {}, 0});
+    for (int i = 0; i < 10; ++i) ops.push_back({0, i % 2, (i + 1) % 2, {}, 0, 0});
     return ops;
   }
-  for (int i = 0; i < m; ++i) ops.push_back({0, i % 2, (i + 1) % 2, {}, 0});
+  for (int i = 0; i < m; ++i) ops.push_back({0, i % 2, (i + 1) % 2, {}, 0, 0});
   const int base = m % 2;   // slot of x_m
-  for (int j = 0; j < k; ++j) ops.push_back({0, base + j, base + j + 1, {}, 0});
-  CycleOp v{1, 0, 0, {}, 0};
+  for (int j = 0; j < k; ++j)
+    ops.push_back({0, base + j, base + j + 1, {}, 0, (freeze > 0 && j == k - 1) ? 1 : 0});
+  CycleOp v{1, 0, 0, {}, 0, freeze > 0 ? 1 : 0};
   for (int j = 0; j <= k; ++j) v.slots.push_back(base + j);
   v.out = 0;
   ops.push_back(v);
@@ -408,6 +428,8 @@ static void fill_prob_dev(red_problem_s *P) {
   d.cg_iters = c.cg_iters;
   d.ve_k = c.ve_k;
   d.ve_method = c.ve;
+  d.baseline = c.baseline == RED_BASE_SD ? kBaseSD : kBaseFP;
+  d.ve_freeze = c.ve_freeze;
   d.inv_sigma2 = (float)(1.0 / (c.sigma * c.sigma));
   d.alpha = (float)c.alpha;
   d.nlm_k = (float)std::sqrt(1.4426950408889634074 / (25.0 * c.nlm_h * c.nlm_h));
@@ -432,6 +454,7 @@ static void fill_prob_dev(red_problem_s *P) {
     d.cg_z = reinterpret_cast<float *>(b + L.cz);
   }
   d.psf = reinterpret_cast<const float *>(b + L.psf);
+  d.sd = reinterpret_cast<SdParams *>(b + L.sd);
   d.row_stats = reinterpret_cast<float2 *>(b + L.row_stats);
   d.gram_part = reinterpret_cast<double *>(b + L.gram);
   d.ve_coef = reinterpret_cast<double *>(b + L.coef);
@@ -458,6 +481,13 @@ void red::problem_precompute(red_problem_s *P, cudaStream_t s) {
   ProbDev &d = P->pd;
   char *b = static_cast<char *>(P->block);
   float *y = reinterpret_cast<float *>(b + P->L.y);
+  const bool sd = c.baseline == RED_BASE_SD;
+  if (sd && !P->sd_ready) {
+    // the SD step size depends on the PSF and the physics only (once per problem)
+    CUDA_OK(launch_sd_step_size(P->d_pd, d.psf, c.psf_h, c.psf_w, d.H, d.W,
+                                1.0 / (c.sigma * c.sigma), c.alpha, c.sd_mu, d.sd, s));
+    P->sd_ready = true;
+  }
   if (c.task == RED_DEBLUR) {
     const Plan &pl = P->plan3;
     float2 *kh = const_cast<float2 *>(d.Kh);
@@ -485,7 +515,7 @@ void red::problem_precompute(red_problem_s *P, cudaStream_t s) {
     CUDA_OK(launch_spectral_constants(P->d_pd, d.Kh, d.spec, const_cast<float2 *>(d.Cc),
                                       const_cast<float *>(d.Gg), d.H * d.Wh,
                                       1.0 / (c.sigma * c.sigma), c.alpha,
-                                      1.0 / ((double)d.H * d.W), s));
+                                      1.0 / ((double)d.H * d.W), s, sd ? d.sd : nullptr));
   } else {
     CUDA_OK(launch_sr_rhs(P->d_pd, y, s));
   }
@@ -581,15 +611,18 @@ red_status red_denoise(red_problem p, const void *x_dev, void *f_dev, void *stre
     StepArgs sa{0, 0, x_dev, nullptr, 0};
     CUDA_OK(launch_nlm(p->d_pd, p->plan.d_items + p->plan.off_nlm, p->plan.n_nlm,
                        p->plan.lc.nlm_wy, sa, 0, static_cast<cudaStream_t>(stream),
-                       static_cast<float *>(f_dev)));
+                       static_cast<float *>(f_dev), p->plan.lc.nlm_occ));
     return RED_OK;
   });
 }
+
+static bool aligned8(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 7) == 0; }
 
 red_status red_fp_step(red_problem p, const void *x_in_dev, void *x_out_dev, void *stream) {
   return guarded([&] {
     CHECK_ARG(p && x_in_dev && x_out_dev, "null argument");
     CHECK_ARG(x_in_dev != x_out_dev, "x_in and x_out must be distinct buffers");
+    CHECK_ARG(aligned8(x_in_dev) && aligned8(x_out_dev), "x_in and x_out must be 8-byte aligned");
     StepArgs sa{0, 0, x_in_dev, static_cast<float *>(x_out_dev), 0};
     launch_fp_step(p->d_pd, p->plan, sa, 0, static_cast<cudaStream_t>(stream));
     return RED_OK;
@@ -629,6 +662,7 @@ red_status red_ve_extrapolate(red_problem p, const void *const *xs_dev, int n_ve
 red_status red_objective(red_problem p, const void *x_dev, double *e_host, void *stream) {
   return guarded([&] {
     CHECK_ARG(p && x_dev && e_host, "null argument");
+    CHECK_ARG(aligned8(x_dev), "x must be 8-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float *x = static_cast<const float *>(x_dev);
     char *b = static_cast<char *>(p->block);
@@ -638,7 +672,7 @@ red_status red_objective(red_problem p, const void *x_dev, double *e_host, void 
     // f(x) into the problem's f buffer
     StepArgs sa{0, 0, x, nullptr, 0};
     CUDA_OK(launch_nlm(p->d_pd, p->plan.d_items + p->plan.off_nlm, p->plan.n_nlm,
-                       p->plan.lc.nlm_wy, sa, 0, s));
+                       p->plan.lc.nlm_wy, sa, 0, s, nullptr, p->plan.lc.nlm_occ));
     const float *hx = nullptr;
     if (p->cfg.task == RED_DEBLUR) {
       const Plan &pl = p->plan3;

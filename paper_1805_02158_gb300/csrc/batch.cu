@@ -104,7 +104,7 @@ std::string tune_key(const red_batch_s *b) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  key << "v4|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  key << "v5|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
   for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
   std::string k = key.str();
   std::replace(k.begin(), k.end(), ' ', '_');
@@ -172,14 +172,14 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
     for (int q : {16, 8, 4, 0}) {
       c.fft_cluster = q;
       if (q > 0) {
-        int ac = 0, bc = 0, tm = 0, th = 0, aa = 0, bb = 0;
+        int ac = 0, bc = 0, cgc = 0, tm = 0, th = 0, aa = 0, bb = 0;
         for (auto *p : b->probs)
           if (p->cfg.task == RED_DEBLUR) {
-            fft_cluster_caps(p->pd.H, p->pd.W, q, &ac, &bc);
+            fft_cluster_caps(p->pd.H, p->pd.W, q, &ac, &bc, &cgc);
             tm = std::max(tm, p->pd.M); th = std::max(th, p->pd.H);
             aa = std::max(aa, ac); bb = std::max(bb, bc);
           }
-        const int smem = std::min(fft_cluster_smem(tm, th, aa, bb), 220 * 1024);
+        const int smem = std::min(fft_cluster_smem(tm, th, aa, bb, 0), 220 * 1024);
         if (fft_cluster_prepare(smem, q) != cudaSuccess || fft_cluster_max_active(q, smem) < 1) {
           cudaGetLastError();
           continue;
@@ -266,7 +266,7 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
   PhaseScope ps{b, s, b->phase_next};
   for (const CycleOp &op : b->ops) {
     if (op.kind == 0) {
-      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
+      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1, op.skip_frozen};
       ps.begin(RED_PHASE_NLM);
       CUDA_OK(launch_nlm(b->d_pds, pl.d_items + pl.off_nlm, pl.n_nlm, pl.lc.nlm_wy, sa, 0, s,
                          nullptr, pl.lc.nlm_occ));
@@ -287,14 +287,17 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
       va.nvec = (int)op.slots.size();
       va.out_slot = op.out;
       va.update_state = 1;
+      va.skip_frozen = op.skip_frozen;
       ps.begin(RED_PHASE_GRAM);
       CUDA_OK(launch_gram(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
       ps.end();
       ps.begin(RED_PHASE_VESOLVE);
-      CUDA_OK(launch_ve_solve(b->d_pds, n, va.nvec, va.update_state, s));
+      CUDA_OK(launch_ve_solve(b->d_pds, n, va.nvec, va.update_state, s, va.skip_frozen));
       ps.end();
       ps.begin(RED_PHASE_COMBINE);
-      CUDA_OK(launch_combine(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
+      VeArgs vc = va;
+      vc.skip_frozen = 0;   // frozen problems combine with their stored xi
+      CUDA_OK(launch_combine(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, vc, s));
       ps.end();
     }
   }
@@ -363,9 +366,11 @@ red_batch_s *batch_new(const red_problem *problems, int n) {
   b->ve = c0.ve;
   b->k = c0.ve_k;
   b->m = c0.ve_m;
+  b->freeze = c0.ve_freeze;
   for (auto *p : b->probs)
-    CHECK_ARG(p->cfg.ve == b->ve && p->cfg.ve_k == b->k && p->cfg.ve_m == b->m,
-              "all problems of a batch need the same ve, ve_k and ve_m");
+    CHECK_ARG(p->cfg.ve == b->ve && p->cfg.ve_k == b->k && p->cfg.ve_m == b->m &&
+                  p->cfg.ve_freeze == b->freeze,
+              "all problems of a batch need the same ve, ve_k, ve_m and ve_freeze");
   for (auto *p : b->probs) b->pds.push_back(p->pd);
   CUDA_OK(cudaMalloc(&b->d_pds, sizeof(ProbDev) * n));
   CUDA_OK(cudaMalloc(&b->d_states, sizeof(ProbState) * n));
@@ -373,7 +378,7 @@ red_batch_s *batch_new(const red_problem *problems, int n) {
   CUDA_OK(cudaMalloc(&b->d_ptrs, sizeof(float *) * 2 * n));
   CUDA_OK(cudaMallocHost(&b->h_states, sizeof(ProbState) * n));
   CUDA_OK(cudaMallocHost(&b->h_ptrs, sizeof(float *) * 2 * n));
-  b->ops = cycle_ops(b->ve, b->k, b->m);
+  b->ops = cycle_ops(b->ve, b->k, b->m, b->freeze);
   b->fp_per_cycle = 0;
   for (auto &op : b->ops) b->fp_per_cycle += op.kind == 0;
   b->tune_key = tune_key(b.get());
@@ -402,10 +407,14 @@ red_status batch_solve_impl(red_batch_s *b, const void *const *x0, int max_calls
   CUDA_OK(launch_copy_slots(b->d_pds, b->plan.d_items + b->plan.off_chunks, b->plan.n_chunks, 0, 0,
                             b->d_ptrs, s));
   b->phase_next = 0;
-  const int max_cycles = max_calls <= 0 ? 0 : (max_calls + b->fp_per_cycle - 1) / b->fp_per_cycle;
+  // a frozen cycle makes one FP step fewer: the budget may need more cycles than the
+  // full-cycle count, after which the states are read back every cycle
+  const int full_cycles = max_calls <= 0 ? 0 : (max_calls + b->fp_per_cycle - 1) / b->fp_per_cycle;
+  const int min_steps = b->freeze > 0 ? b->fp_per_cycle - 1 : b->fp_per_cycle;
+  const int max_cycles = max_calls <= 0 ? 0 : (max_calls + min_steps - 1) / min_steps;
   for (int c = 0; c < max_cycles; ++c) {
     run_cycle(b, s);
-    if (tol > 0.0 && c + 1 < max_cycles) {
+    if ((tol > 0.0 || c + 1 >= full_cycles) && c + 1 < max_cycles) {
       CUDA_OK(cudaMemcpyAsync(b->h_states, b->d_states, sizeof(ProbState) * n, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
       bool all = true;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace red {
 
@@ -15,6 +16,7 @@ constexpr int kMaxPairs = kMaxK * (kMaxK + 1) / 2;
 constexpr int kGramChunk = 2048;                // pixels per Gram / combine work unit
 constexpr int kNlmR = 6;                        // output rows per NLM thread
 constexpr int kNlmTW = 60;                      // output columns per NLM warp (64 - 4 halo)
+
 constexpr double kRankTol = 1e-12;              // rank-loss threshold on r_jj^2 / ||u_j||^2
 constexpr double kSumTol = 1e-12;               // MPE existence: |sum c| > tol * sum |c|
 
@@ -42,6 +44,17 @@ struct ProbState {
   int frozen;          // 1 once ve_ok reached ve_freeze: later cycles reuse xi
   int solved;          // 1 between a gamma solve and the combine that uses it
   int frozen_steps;    // combines with the frozen xi
+};
+
+// Step size of the steepest-descent baseline: mu = 1 / (max |K(w)|^2 / sigma^2 + alpha)
+// unless the config gives one. Written by the set-up kernels, read by the step kernels.
+struct SdParams {
+  double mu;               // FP64 (the spectral constants are formed in FP64)
+  float mu_f;              // mu and mu * alpha in FP32 (the step epilogues)
+  float mu_alpha_f;
+  unsigned int kmax_bits;  // bits of max |K(w)|^2 as a float (non-negative floats order
+                           // as unsigned integers, so atomicMax on the bits takes the max)
+  unsigned int pad;
 };
 
 // Everything a kernel needs to know about one problem. Plain data, copied to device
@@ -76,9 +89,8 @@ struct ProbDev {
   const float *b0;        // H^T y / sigma^2 (N)
   float *cg_x, *cg_r, *cg_p, *cg_ap, *cg_z;   // CG vectors; z is LR sized
   const float *psf;       // kh x kw taps
-  // steepest descent (baseline kBaseSD): (mu, mu * alpha), computed on the device
-  float2 *sd;
-  unsigned int *sd_kmax;  // bits of max |K(w)|^2 (non-negative floats order as integers)
+  // steepest descent (baseline kBaseSD): the step size, set up on the device
+  struct SdParams *sd;
   // extrapolation
   double *gram_part;      // n_chunks x kMaxPairs
   double *ve_coef;        // kMaxK: xi_j of Algorithm 1 step 3 (difference form), + gamma
@@ -120,30 +132,38 @@ struct LaunchCfg {
   int fft_cluster = 16;    // CTAs per cluster of the fused Fourier solve (0: three passes)
 };
 
-// NLM over the items: reads slot sa.src (or sa.src_ptr), writes f_override or each
-// problem's f buffer.
+// NLM over the items: reads slot sa.src (or sa.src_ptr), writes f_override (if non-null) or
+// each problem's f buffer.
 cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items, int wy,
-                       StepArgs sa, int src_type, cudaStream_t s,
-                       float *f_override = nullptr, int occ = 4);
+                       StepArgs sa, int src_type, cudaStream_t s, float *f_override, int occ);
 // FFT launches: items carry (prob, first row/col, count). tw_cap = largest transform
 // length in the launch (M for rows, H for columns); buf_cap = largest per-item buffer
 // (rows * M, or cols * (H + 1)) in complex elements.
+// step: null for transforms of a given image (set-up, objective); the FP step's slots
+// otherwise (an SD problem's step transforms x_k instead of f).
 cudaError_t launch_fft_r2c(const ProbDev *d_probs, const Item *d_items, int n_items,
                            int tw_cap, int buf_cap, const float *src_override,
-                           float2 *dst_override, int skip_done, cudaStream_t s);
+                           float2 *dst_override, int skip_done, cudaStream_t s,
+                           const StepArgs *step = nullptr);
 cudaError_t launch_fft_cols(const ProbDev *d_probs, const Item *d_items, int n_items,
                             int tw_cap, int buf_cap, int mode, float2 *spec_override,
                             int skip_done, cudaStream_t s);
 cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_items,
                            int tw_cap, int buf_cap, StepArgs sa, cudaStream_t s);
+// sd: null for the FP solve's C and G, else the SD step's constants with its step size.
 cudaError_t launch_spectral_constants(const ProbDev *d_prob, const float2 *k_hat,
                                       const float2 *y_hat, float2 *Cc, float *Gg, int n,
                                       double inv_sigma2, double alpha, double inv_hw,
-                                      cudaStream_t s);
+                                      cudaStream_t s, const SdParams *sd = nullptr);
+// The SD step size of one problem into P->sd: max |K(w)|^2 over the H x (W/2 + 1) half
+// spectrum by direct evaluation of the PSF's DFT, then mu (mu_given > 0 overrides).
+cudaError_t launch_sd_step_size(const ProbDev *d_prob, const float *psf, int kh, int kw, int H,
+                                int W, double inv_sigma2, double alpha, double mu_given,
+                                SdParams *sd, cudaStream_t s);
 cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items,
                         const VeArgs &va, cudaStream_t s);
 cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec,
-                            int update_state, cudaStream_t s);
+                            int update_state, cudaStream_t s, int skip_frozen = 0);
 cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
                            const VeArgs &va, cudaStream_t s);
 cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n_items,
@@ -174,13 +194,16 @@ cudaError_t launch_objective(const ProbDev *d_prob, const float *x, const float 
                              const float *y, const float *f, double *out, cudaStream_t s);
 
 // Cluster solve (one cluster per deblurring problem, spectrum in shared memory).
-void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems);
-int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap);
+void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems, int *cg_elems);
+int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap, int cg_cap);
+// Shared memory per CTA of the cluster solve up to which two CTAs fit on an SM (the C/G
+// staging is dropped above it, so the 16-CTA clusters of every problem stay resident).
+constexpr int kClusterSmemTwoPerSm = 112 * 1024;
 cudaError_t fft_cluster_prepare(int smem, int ncta);
 int fft_cluster_max_active(int ncta, int smem);
 cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, int n, int ncta,
                                      int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap,
-                                     StepArgs sa, cudaStream_t s);
+                                     int cg_cap, StepArgs sa, cudaStream_t s);
 int fft_smem_rows(int tw_cap, int buf_cap);
 int fft_smem_cols(int tw_cap, int buf_cap);
 
@@ -190,7 +213,24 @@ cudaError_t sr_prepare(int cluster, int smem);
 int sr_max_active_clusters(int cluster, int smem, int spec737, int minb);
 cudaError_t nlm_prepare(int wy);
 
+// NLM work items of one image (nlm.cu).
+void nlm_items(int prob, int H, int W, std::vector<Item> &out);
+
 // ---- small device helpers ---------------------------------------------------------------
+// Division by a run-time invariant d < 2^16 for numerators t < 2^16: q = hi32(t * m) with
+// m = floor(2^32 / d) + 1 (exact in that range; d = 1 handled separately). Every index
+// divided with it is below 2^16 (image sides <= 2048, <= 16 sequences per FFT CTA).
+struct FastDiv {
+  uint32_t d, m;
+  __device__ __forceinline__ explicit FastDiv(int dd)
+      : d((uint32_t)dd), m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
+  __device__ __forceinline__ int div(int t) const { return d == 1 ? t : (int)__umulhi((uint32_t)t, m); }
+  __device__ __forceinline__ void divmod(int t, int &q, int &r) const {
+    q = div(t);
+    r = t - q * (int)d;
+  }
+};
+
 // Stride of one transform sequence of length n in shared memory: one pad slot per 16
 // elements, rounded up to odd (bank-conflict-free strided and transposed accesses).
 __host__ __device__ __forceinline__ int fft_seq_stride(int n) { return (n + (n >> 4)) | 1; }

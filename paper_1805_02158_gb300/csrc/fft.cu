@@ -22,6 +22,12 @@
 // Sequences in shared memory are padded (one slot per 16 elements, odd stride) so the
 // strided Stockham writes and the column transposes are free of bank conflicts.
 // Inverse transforms use IFFT(X) = conj(FFT(conj(X))); the 1/(H W) scale is in C and G.
+//
+// The same transforms serve the steepest-descent baseline of SD-MPE (Sec. IV): one SD step
+// on Eq. (5) for a circulant H is
+//   x_{k+1} = x_k - mu grad E(x_k) = IFFT2( C_sd + G_sd . FFT2(x_k) ) + mu alpha f(x_k),
+//   C_sd = mu conj(K) FFT2(y) / sigma^2 / (H W),  G_sd = (1 - mu alpha - mu |K|^2 / sigma^2) / (H W),
+// so an SD problem's step transforms x_k instead of f and adds mu alpha f at the output.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -34,6 +40,21 @@ namespace red {
 
 namespace {
 
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes, source aligned to the size):
+// each thread issues its copies, commits them as a group, and waits for the group before a
+// barrier, so all loads of a phase are in flight together and land in any shared layout.
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -42,20 +63,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // * (-i)
 __device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); }  // * (+i)
-
-// Division by a run-time invariant d < 2^16 for numerators t < 2^16: q = hi32(t * m) with
-// m = floor(2^32 / d) + 1 (exact in that range; d = 1 handled separately). Every index
-// divided here is below 2^16 (image sides <= 2048, <= 16 sequences per CTA).
-struct FastDiv {
-  uint32_t d, m;
-  __device__ __forceinline__ explicit FastDiv(int dd)
-      : d((uint32_t)dd), m(dd > 1 ? 0xFFFFFFFFu / (uint32_t)dd + 1u : 0u) {}
-  __device__ __forceinline__ int div(int t) const { return d == 1 ? t : (int)__umulhi((uint32_t)t, m); }
-  __device__ __forceinline__ void divmod(int t, int &q, int &r) const {
-    q = div(t);
-    r = t - q * (int)d;
-  }
-};
 
 // e^{-2 pi i m / 48}: every root of unity the radix-16/12/8/6 kernels need
 __device__ __forceinline__ float2 root48(int m) {
@@ -315,6 +322,13 @@ struct StepOut {
   __device__ __forceinline__ float2 prev(long base) const {
     return make_float2(load_img(src_ring, base, src_type), load_img(src_ring, base + 1, src_type));
   }
+  // mu alpha f at (base, base + 1) for an SD problem's step output, 0 for an FP step
+  __device__ __forceinline__ float2 sd_term(long base) const {
+    if (P->baseline != kBaseSD) return make_float2(0.f, 0.f);
+    const float ma = P->sd->mu_alpha_f;
+    const float2 fv = *reinterpret_cast<const float2 *>(P->f + base);
+    return make_float2(ma * fv.x, ma * fv.y);
+  }
   // writes x_{k+1}[base], [base+1] = (xe, xo); accumulates the statistics against pv
   __device__ __forceinline__ void put(long base, float xe, float xo, float2 pv, float &sd,
                                       float &sx) const {
@@ -353,11 +367,13 @@ __device__ __forceinline__ void finish_step(ProbState *st, double sd, double sx,
 // Pass 1: rows, real to half spectrum. Item (prob, first row, rows).
 __global__ void __launch_bounds__(256)
 k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int tw_cap,
-          int buf_cap, const float *src_override, float2 *dst_override, int skip_done) {
+          int buf_cap, const float *src_override, float2 *dst_override, int skip_done,
+          StepArgs sa, int is_step) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
-  if (skip_done && P->st->done) return;
+  if ((skip_done & 1) && P->st->done) return;     // bit 0: finished problems
+  if ((skip_done & 2) && P->st->frozen) return;   // bit 1: frozen problems (full-cycle step)
   const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
   const int ss = fft_seq_stride(M);
   const int r0 = it.a;
@@ -370,11 +386,16 @@ k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
   const float *src = src_override ? src_override : P->f;
+  // an SD problem's step transforms x_k (its ring slot, any storage type)
+  const bool sd_step = is_step && P->baseline == kBaseSD;
+  StepOut xin;
+  if (sd_step) xin.init(P, sa);
   const FastDiv dm(M), dwh(Wh);
   copy_batched<4>(nr * M, tid, nthr,
       [&](int idx) {
         int row, n;
         dm.divmod(idx, row, n);
+        if (sd_step) return xin.prev((long)(r0 + row) * W + 2 * n);
         return reinterpret_cast<const float2 *>(src + (long)(r0 + row) * W)[n];
       },
       [&](int idx, float2 v) {
@@ -401,7 +422,8 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
-  if (skip_done && P->st->done) return;
+  if ((skip_done & 1) && P->st->done) return;     // bit 0: finished problems
+  if ((skip_done & 2) && P->st->frozen) return;   // bit 1: frozen problems (full-cycle step)
   const int H = P->H, Wh = P->Wh;
   const int c0 = it.a;
   const int nc = min(it.b, Wh - c0);
@@ -470,6 +492,7 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (sa.update_state && P->st->done) return;
+  if (sa.skip_frozen && P->st->frozen) return;
   const int M = P->M, W = P->W, H = P->H, Wh = P->Wh;
   const int ss = fft_seq_stride(M);
   const int r0 = it.a;
@@ -501,7 +524,8 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
     float sd = 0.f, sx = 0.f;
     for (int n = lane; n < M; n += 32) {
       const float2 v = Y[row * ss + pidx(n)];
-      out.put(rowbase + 2 * n, v.x, -v.y, out.prev(rowbase + 2 * n), sd, sx);
+      const float2 t = out.sd_term(rowbase + 2 * n);
+      out.put(rowbase + 2 * n, v.x + t.x, -v.y + t.y, out.prev(rowbase + 2 * n), sd, sx);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -563,7 +587,7 @@ __device__ __forceinline__ int band_owner(int h, int ncta, const FastDiv &by_n) 
 
 __global__ void __launch_bounds__(kClusterThreads, 2)
 k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ list, StepArgs sa,
-                    int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
+                    int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap, int cg_cap) {
   extern __shared__ float2 sm[];
   __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
   __shared__ int is_last;
@@ -571,7 +595,9 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
   const ProbDev *P = probs + list[blockIdx.x / ncta];
-  if (sa.update_state && P->st->done) return;   // uniform over the cluster
+  // both tests are uniform over the cluster (one problem per cluster)
+  if (sa.update_state && P->st->done) return;
+  if (sa.skip_frozen && P->st->frozen) return;
   const int H = P->H, W = P->W, M = P->M, Wh = P->Wh;
   const int ssm = fft_seq_stride(M), ssh = fft_seq_stride(H);
   const FastDiv by_ncta(ncta), by_h(H);
@@ -586,44 +612,44 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   float2 *Rb = X1 + buf_cap;        // this CTA's spectrum columns, pushed by every band
   const int tid = threadIdx.x, nthr = blockDim.x;
   const FastDiv fdm(M), fdwh(Wh), fdc(nc > 0 ? nc : 1);
-  // x_k for the statistics, fetched first (its latency hides behind the transforms)
-  constexpr int kPrev = 4;
-  float2 prev[kPrev];
   StepOut out;
   out.init(P, sa);
-#pragma unroll
-  for (int u = 0; u < kPrev; ++u) {
-    const int idx = tid + u * nthr;
-    if (idx < nr * M) {
+  // 1. group 0: twiddle tables and the band's rows (f, or x_k for an SD step) straight into
+  //    the padded row buffer; group 1 (when cg_cap > 0): C and G of the CTA's columns, needed
+  //    only after the column transform, so their latency hides behind it
+  const bool sd_step = P->baseline == kBaseSD;
+  for (int i = tid; i < M; i += nthr) cp_async8(twm + i, P->tw_m + i);
+  for (int i = tid; i <= M; i += nthr) cp_async8(tww + i, P->tw_w + i);
+  for (int i = tid; i < H; i += nthr) cp_async8(twh + i, P->tw_h + i);
+  if (!sd_step || out.src_type == kStoreF32) {
+    const float *rows = sd_step ? static_cast<const float *>(out.src_ring) : P->f;
+    for (int idx = tid; idx < nr * M; idx += nthr) {
       int row, n;
       fdm.divmod(idx, row, n);
-      prev[u] = out.prev((long)(r0 + row) * W + 2 * n);
+      cp_async8(X0 + row * ssm + pidx(n), rows + (long)(r0 + row) * W + 2 * n);
+    }
+  } else {   // SD step from a 16-bit ring: converted on the way in
+    for (int idx = tid; idx < nr * M; idx += nthr) {
+      int row, n;
+      fdm.divmod(idx, row, n);
+      X0[row * ssm + pidx(n)] = out.prev((long)(r0 + row) * W + 2 * n);
     }
   }
-  // twiddle tables and the band's rows of f, all loads in flight together
-  const int ntw = M + (M + 1) + H;
-  copy_batched<8>(ntw + nr * M, tid, nthr,
-      [&](int idx) {
-        if (idx < M) return P->tw_m[idx];
-        if (idx < 2 * M + 1) return P->tw_w[idx - M];
-        if (idx < ntw) return P->tw_h[idx - 2 * M - 1];
-        int row, n;
-        fdm.divmod(idx - ntw, row, n);
-        return reinterpret_cast<const float2 *>(P->f + (long)(r0 + row) * W)[n];
-      },
-      [&](int idx, float2 v) {
-        if (idx < M) {
-          twm[idx] = v;
-        } else if (idx < 2 * M + 1) {
-          tww[idx - M] = v;
-        } else if (idx < ntw) {
-          twh[idx - 2 * M - 1] = v;
-        } else {
-          int row, n;
-          fdm.divmod(idx - ntw, row, n);
-          X0[row * ssm + pidx(n)] = v;
-        }
-      });
+  cp_async_commit();
+  float2 *Cs = Rb + buf_cap;                              // cg_cap complex C values
+  float *Gs = reinterpret_cast<float *>(Cs + cg_cap);     // cg_cap real G values
+  const bool cg_staged = cg_cap >= H * nc;
+  if (cg_staged) {
+    for (int idx = tid; idx < H * nc; idx += nthr) {
+      int r, c;
+      fdc.divmod(idx, r, c);
+      const long g = (long)r * Wh + c0 + c;
+      cp_async8(Cs + idx, P->Cc + g);
+      cp_async4(Gs + idx, P->Gg + g);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait<1>();   // group 0 landed (group 1 may still be in flight)
   __syncthreads();
   const float2 *Z = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
   // 2. push: every half-spectrum bin of the band's rows goes straight into the column
@@ -640,6 +666,10 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   }
   cl.sync();
   float2 *F = fft_smem(Rb, X0, H, nc, ssh, twh, tid, nthr);
+  if (cg_staged) {
+    cp_async_wait<0>();
+    __syncthreads();
+  }
   for (int base = tid; base < H * nc; base += 4 * nthr) {
     float2 cc[4];
     float gg[4];
@@ -647,11 +677,16 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     for (int u = 0; u < 4; ++u) {
       const int idx = base + u * nthr;
       if (idx < H * nc) {
-        int r, c;
-        fdc.divmod(idx, r, c);
-        const long g = (long)r * Wh + c0 + c;
-        cc[u] = P->Cc[g];
-        gg[u] = P->Gg[g];
+        if (cg_staged) {
+          cc[u] = Cs[idx];
+          gg[u] = Gs[idx];
+        } else {
+          int r, c;
+          fdc.divmod(idx, r, c);
+          const long g = (long)r * Wh + c0 + c;
+          cc[u] = P->Cc[g];
+          gg[u] = P->Gg[g];
+        }
       }
     }
 #pragma unroll
@@ -677,7 +712,21 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     Aq[(h - band_lo(q, H, by_ncta)) * Wh + c0 + c] = cconj(Xs[c * ssh + pidx(h)]);
   }
   cl.sync();
-  // 4. rows, half spectrum to real, statistics against x_k
+  // 4. x_k of the band for the statistics into Rb (free since the barrier: every CTA has
+  //    finished reading its columns), in flight during the inverse row transform; then rows,
+  //    half spectrum to real, statistics against x_k
+  const int esz = store_bytes(out.src_type);
+  char *prev_s = reinterpret_cast<char *>(Rb);
+  {
+    const char *src = static_cast<const char *>(out.src_ring) + (size_t)r0 * W * esz;
+    for (int idx = tid; idx < nr * M; idx += nthr) {
+      if (esz == 4)
+        cp_async8(prev_s + 8 * idx, src + 8 * (size_t)idx);
+      else
+        cp_async4(prev_s + 4 * idx, src + 4 * (size_t)idx);
+    }
+    cp_async_commit();
+  }
   for (int idx = tid; idx < nr * M; idx += nthr) {
     int row, kk;
     fdm.divmod(idx, row, kk);
@@ -685,31 +734,18 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   }
   __syncthreads();
   const float2 *Y = fft_smem(X0, X1, M, nr, ssm, twm, tid, nthr);
+  cp_async_wait<0>();
+  __syncthreads();
   float sd = 0.f, sx = 0.f;
-  for (int b0 = tid; b0 < nr * M; b0 += kPrev * nthr) {
-    float2 pv[kPrev];
-#pragma unroll
-    for (int u = 0; u < kPrev; ++u) {
-      const int idx = b0 + u * nthr;
-      if (idx < nr * M) {
-        if (b0 == tid) {
-          pv[u] = prev[u];
-        } else {
-          int row, n;
-          fdm.divmod(idx, row, n);
-          pv[u] = out.prev((long)(r0 + row) * W + 2 * n);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kPrev; ++u) {
-      const int idx = b0 + u * nthr;
-      if (idx >= nr * M) break;
-      int row, n;
-      fdm.divmod(idx, row, n);
-      const float2 v = Y[row * ssm + pidx(n)];
-      out.put((long)(r0 + row) * W + 2 * n, v.x, -v.y, pv[u], sd, sx);
-    }
+  for (int idx = tid; idx < nr * M; idx += nthr) {
+    int row, n;
+    fdm.divmod(idx, row, n);
+    const float2 v = Y[row * ssm + pidx(n)];
+    const long e = (long)(r0 + row) * W + 2 * n;
+    const float2 pv = make_float2(load_img(prev_s, 2 * (long)idx, out.src_type),
+                                  load_img(prev_s, 2 * (long)idx + 1, out.src_type));
+    const float2 t = out.sd_term(e);
+    out.put(e, v.x + t.x, -v.y + t.y, pv, sd, sx);
   }
   // CTA sums (fixed order); the per-CTA partials are summed below by the last CTA to arrive
   const int lane = tid & 31, warp = tid >> 5;
@@ -751,18 +787,72 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
   }
 }
 
+// FP solve (sd == null): C = conj(K) Y / (sigma^2 D) / (H W), G = alpha / D / (H W) with
+// D = |K|^2 / sigma^2 + alpha. SD step: C_sd = mu conj(K) Y / sigma^2 / (H W),
+// G_sd = (1 - mu alpha - mu |K|^2 / sigma^2) / (H W).
 __global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,
                                      float2 *Cc, float *Gg, int n, double inv_sigma2,
-                                     double alpha, double inv_hw) {
+                                     double alpha, double inv_hw, const SdParams *sd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double kr = khat[i].x, ki = khat[i].y;
   const double yr = yhat[i].x, yi = yhat[i].y;
-  const double d = (kr * kr + ki * ki) * inv_sigma2 + alpha;
+  const double k2 = kr * kr + ki * ki;
   // conj(K) Y = (kr yr + ki yi) + i (kr yi - ki yr)
-  const double s = inv_sigma2 / d * inv_hw;
+  double s, g;
+  if (sd) {
+    const double mu = sd->mu;
+    s = mu * inv_sigma2 * inv_hw;
+    g = (1.0 - mu * alpha - mu * k2 * inv_sigma2) * inv_hw;
+  } else {
+    const double d = k2 * inv_sigma2 + alpha;
+    s = inv_sigma2 / d * inv_hw;
+    g = alpha / d * inv_hw;
+  }
   Cc[i] = make_float2((float)((kr * yr + ki * yi) * s), (float)((kr * yi - ki * yr) * s));
-  Gg[i] = (float)(alpha / d * inv_hw);
+  Gg[i] = (float)g;
+}
+
+// max |K(w)|^2 over the half spectrum (rows u < H, columns v <= W/2), K the DFT of the
+// PSF taps, evaluated directly: K(u, v) = sum_{a, b} psf[a][b] e^{-2 pi i (u a / H + v b / W)}
+// (|K| does not depend on where the PSF is centred). The phase is reduced exactly in
+// integers (t = (u a mod H) W + (v b mod W) H over H W, below 2^23), so FP32 keeps it to
+// rounding. Each thread takes frequencies by a grid stride and folds its maximum into the
+// bits of sd->kmax_bits.
+__global__ void __launch_bounds__(256)
+k_psf_spectrum_max(const float *__restrict__ psf, int kh, int kw, int H, int W, SdParams *sd) {
+  const int Wh = W / 2 + 1;
+  const long nf = (long)H * Wh;
+  const float inv_hw2 = 2.0f / ((float)H * (float)W);
+  float best = 0.f;
+  for (long f = blockIdx.x * (long)blockDim.x + threadIdx.x; f < nf; f += (long)gridDim.x * blockDim.x) {
+    const int u = (int)(f / Wh), v = (int)(f - (long)u * Wh);
+    float re = 0.f, im = 0.f;
+    for (int a = 0; a < kh; ++a) {
+      const int pu = (int)(((long)u * a) % H) * W;
+      for (int b = 0; b < kw; ++b) {
+        const int t = pu + (int)(((long)v * b) % W) * H;   // < 2 H W
+        float sn, cs;
+        sincospif((float)t * inv_hw2, &sn, &cs);
+        const float w = psf[a * kw + b];
+        re = fmaf(w, cs, re);
+        im = fmaf(-w, sn, im);
+      }
+    }
+    best = fmaxf(best, fmaf(re, re, im * im));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&sd->kmax_bits, __float_as_uint(best));
+}
+
+// mu = 1 / (max |K|^2 / sigma^2 + alpha), or the configured step size.
+__global__ void k_sd_finish(SdParams *sd, double inv_sigma2, double alpha, double mu_given) {
+  const double kmax = (double)__uint_as_float(sd->kmax_bits);
+  const double mu = mu_given > 0.0 ? mu_given : 1.0 / (kmax * inv_sigma2 + alpha);
+  sd->mu = mu;
+  sd->mu_f = (float)mu;
+  sd->mu_alpha_f = (float)(mu * alpha);
 }
 
 }  // namespace
@@ -798,13 +888,15 @@ cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col
 
 cudaError_t launch_fft_r2c(const ProbDev *d_probs, const Item *d_items, int n_items,
                            int tw_cap, int buf_cap, const float *src_override,
-                           float2 *dst_override, int skip_done, cudaStream_t s) {
+                           float2 *dst_override, int skip_done, cudaStream_t s,
+                           const StepArgs *step) {
   if (n_items <= 0) return cudaSuccess;
   const int smem = fft_smem_rows(tw_cap, buf_cap);
   cudaError_t e = set_smem((const void *)k_fft_r2c, smem, &hw_r2c);
   if (e != cudaSuccess) return e;
+  const StepArgs sa = step ? *step : StepArgs{};
   k_fft_r2c<<<n_items, 256, smem, s>>>(d_probs, d_items, tw_cap, buf_cap, src_override,
-                                       dst_override, skip_done);
+                                       dst_override, skip_done, sa, step ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -834,16 +926,20 @@ cudaError_t launch_fft_c2r(const ProbDev *d_probs, const Item *d_items, int n_it
 }
 
 // Shared memory of the cluster solve for one problem (complex elements): the row band's
-// half spectrum A, and two work buffers (the band's padded rows or columns).
-void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems) {
+// half spectrum A, two work buffers (the band's padded rows or columns), the column buffer
+// (also the band's x_k at the end), and cg_elems C and G values of the CTA's columns.
+void fft_cluster_caps(int H, int W, int ncta, int *a_elems, int *buf_elems, int *cg_elems) {
   const int M = W / 2, Wh = M + 1;
   const int nr = (H + ncta - 1) / ncta, nc = (Wh + ncta - 1) / ncta;
   *a_elems = nr * Wh;
   *buf_elems = std::max(nr * fft_seq_stride(M), nc * fft_seq_stride(H));
+  *cg_elems = nc * H;
 }
 
-int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap) {
-  return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 3 * (size_t)buf_cap) * sizeof(float2));
+// cg_cap = 0: C and G are read from global memory in the solve phase.
+int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap, int cg_cap) {
+  return (int)(((size_t)2 * tw_cap_m + 1 + tw_cap_h + a_cap + 3 * (size_t)buf_cap) * sizeof(float2) +
+               (size_t)cg_cap * (sizeof(float2) + sizeof(float)));
 }
 
 cudaError_t fft_cluster_prepare(int smem, int ncta) {
@@ -856,12 +952,12 @@ cudaError_t fft_cluster_prepare(int smem, int ncta) {
 
 cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, int n, int ncta,
                                      int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap,
-                                     StepArgs sa, cudaStream_t s) {
+                                     int cg_cap, StepArgs sa, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n * ncta);
   cfg.blockDim = dim3(kClusterThreads);
-  cfg.dynamicSmemBytes = fft_cluster_smem(tw_cap_m, tw_cap_h, a_cap, buf_cap);
+  cfg.dynamicSmemBytes = fft_cluster_smem(tw_cap_m, tw_cap_h, a_cap, buf_cap, cg_cap);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -871,7 +967,7 @@ cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_fft_solve_cluster, d_probs, d_list, sa, tw_cap_m,
-                                     tw_cap_h, a_cap, buf_cap);
+                                     tw_cap_h, a_cap, buf_cap, cg_cap);
   count_launches(1);
   return e;
 }
@@ -899,10 +995,28 @@ int fft_cluster_max_active(int ncta, int smem) {
 
 cudaError_t launch_spectral_constants(const ProbDev *, const float2 *k_hat, const float2 *y_hat,
                                       float2 *Cc, float *Gg, int n, double inv_sigma2,
-                                      double alpha, double inv_hw, cudaStream_t s) {
+                                      double alpha, double inv_hw, cudaStream_t s,
+                                      const SdParams *sd) {
   k_spectral_constants<<<(n + 255) / 256, 256, 0, s>>>(k_hat, y_hat, Cc, Gg, n, inv_sigma2,
-                                                       alpha, inv_hw);
+                                                       alpha, inv_hw, sd);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sd_step_size(const ProbDev *, const float *psf, int kh, int kw, int H, int W,
+                                double inv_sigma2, double alpha, double mu_given, SdParams *sd,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sd, 0, sizeof(SdParams), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long nf = (long)H * (W / 2 + 1);
+  const int ctas = (int)std::min<long>((nf + 255) / 256, 4L * sms);
+  k_psf_spectrum_max<<<ctas, 256, 0, s>>>(psf, kh, kw, H, W, sd);
+  k_sd_finish<<<1, 1, 0, s>>>(sd, inv_sigma2, alpha, mu_given);
+  count_launches(2);
   return cudaGetLastError();
 }
 

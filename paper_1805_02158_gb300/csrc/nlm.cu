@@ -16,13 +16,18 @@
 //   * vertical 5-row sums of squared differences slide down the column with 2 FMAs/row;
 //   * horizontal 5-column sums use 4 warp shuffles per row (the warp covers 64 columns
 //     and outputs the inner 60).
-// Per output pixel and offset: ~8.4 FP32 ops, 1 MUFU.EX2, 2 SHFL; no shared-memory
-// traffic in the inner loop beyond one candidate row per dy.
+// Per output pixel and offset: ~8.7 FP32 ops, 1 MUFU.EX2, 2 SHFL; no shared-memory
+// traffic in the inner loop beyond one candidate row per dy. Two alternatives measured on
+// GB300 and not kept: the same arithmetic in packed f32x2 instructions (no faster:
+// fma.rn.f32x2 has the lane throughput of scalar FMA, 38.2 vs 37.1 T lane-op/s), and the
+// ragged right strip of 256-wide images (16 columns) packed three narrow lane segments to
+// a warp (10.6 % fewer instructions, but a slower busiest SM: 58-61 vs 53 us).
 //
 // Work decomposition is fixed to a (kNlmR-row, 2-column) grid in image coordinates, so a
 // pixel's arithmetic (and result, bit for bit) does not depend on the CTA shape chosen
 // by the autotuner or on which other problems share the launch.
 #include <cstdlib>
+#include <vector>
 
 #include "common.cuh"
 
@@ -60,6 +65,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
   const Item it = items[item];
   const ProbDev *P = probs + it.prob;
   if (sa.update_state && P->st->done) return;
+  if (sa.skip_frozen && P->st->frozen) return;
   float *tile = smem_tiles + threadIdx.y * ((R + 14) * kStride);
 
   const int H = P->H, W = P->W;
@@ -74,8 +80,7 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
     stype = src_type_override;
   } else {
     stype = P->storage;
-    src = static_cast<const char *>(P->ring) +
-          (size_t)sa.src * P->slot_stride * store_bytes(stype);
+    src = static_cast<const char *>(P->ring) + (size_t)sa.src * P->slot_stride * store_bytes(stype);
   }
 
   // Stage the tile: kStageU loads in flight per lane. One reflection is exact for every
@@ -184,170 +189,12 @@ k_nlm(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_i
   }
 }
 
-// Packed-FP32 variant of k_nlm: the lane's two columns travel as one f32x2 register pair
-// through every FP32 add, multiply and FMA (one instruction for both columns), with the
-// same operations in the same order as the scalar kernel, so the results are bit-identical
-// (the patch sums are kept positive instead of negated: IEEE round-to-nearest is symmetric
-// under negation, so each partial sum is the exact negative of the scalar kernel's).
-using f2 = unsigned long long;   // .b64 register pair {column 0, column 1}
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void up(f2 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-template <int R, int MINB>
-__global__ void __launch_bounds__(128, MINB)
-k_nlm_x2(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int n_items, StepArgs sa,
-         int src_type_override, float *f_override) {
-  extern __shared__ float smem_tiles[];
-  const int item = blockIdx.x * blockDim.y + threadIdx.y;
-  if (item >= n_items) return;
-  const Item it = items[item];
-  const ProbDev *P = probs + it.prob;
-  if (sa.update_state && P->st->done) return;
-  float *tile = smem_tiles + threadIdx.y * ((R + 14) * kStride);
-
-  const int H = P->H, W = P->W;
-  const int tr0 = it.a, tc0 = it.b;
-  const int rows = R + 14;
-  const float k = P->nlm_k;
-
-  const void *src;
-  int stype;
-  if (sa.src_ptr) {
-    src = sa.src_ptr;
-    stype = src_type_override;
-  } else {
-    stype = P->storage;
-    src = static_cast<const char *>(P->ring) +
-          (size_t)sa.src * P->slot_stride * store_bytes(stype);
-  }
-
-  // staging: as in k_nlm
-  const int tid = threadIdx.x;
-  const int total = rows * kCols;
-  for (int base = tid; base < total; base += kStageU * 32) {
-    float v[kStageU];
-#pragma unroll
-    for (int u = 0; u < kStageU; ++u) {
-      const int idx = base + u * 32;
-      if (idx < total) {
-        const int rr = idx / kCols;
-        const int cc = idx - rr * kCols;
-        const int gr = reflect_clamp(tr0 - 7 + rr, H);
-        const int gc = reflect_clamp(tc0 - 7 + cc, W);
-        v[u] = load_img(src, (long)gr * W + gc, stype);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kStageU; ++u) {
-      const int idx = base + u * 32;
-      if (idx < total) {
-        const int rr = idx / kCols;
-        tile[rr * kStride + (idx - rr * kCols)] = k * v[u];
-      }
-    }
-  }
-  __syncwarp();
-
-  const int lane = threadIdx.x;
-  const int sc0 = 2 * lane + 5;
-
-  f2 a[R + 4];
-#pragma unroll
-  for (int rr = 0; rr < R + 4; ++rr)
-    a[rr] = pk(tile[(5 + rr) * kStride + sc0], tile[(5 + rr) * kStride + sc0 + 1]);
-  f2 num[R], den[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) num[r] = den[r] = pk(0.f, 0.f);
-
-#pragma unroll 1
-  for (int dx = -5; dx <= 5; ++dx) {
-    const float *bcol = tile + sc0 + dx;
-    f2 b[R + 14];
-#pragma unroll
-    for (int t = 0; t < R + 14; ++t) b[t] = pk(bcol[t * kStride], bcol[t * kStride + 1]);
-#pragma unroll
-    for (int dyi = 0; dyi < 11; ++dyi) {
-      f2 d[R + 4];
-#pragma unroll
-      for (int rr = 0; rr < R + 4; ++rr) d[rr] = sub2(a[rr], b[rr + dyi]);
-      // positive 5-row sums of squared differences
-      f2 v = mul2(d[0], d[0]);
-#pragma unroll
-      for (int t = 1; t < 5; ++t) v = fma2(d[t], d[t], v);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (r > 0) {
-          const f2 e = sub2(b[r - 1 + dyi], a[r - 1]);   // = -d[r - 1], exactly
-          v = fma2(d[r + 4], d[r + 4], fma2(e, d[r - 1], v));
-        }
-        float v0, v1;
-        up(v, v0, v1);
-        const float p = v0 + v1;
-        const float pl = __shfl_up_sync(kFull, p, 1);
-        const float pr = __shfl_down_sync(kFull, p, 1);
-        const float v1l = __shfl_up_sync(kFull, v1, 1);
-        const float v0r = __shfl_down_sync(kFull, v0, 1);
-        float D0, D1;
-        up(add2(add2(pk(pl, v1l), pk(p, p)), pk(v0r, pr)), D0, D1);
-        const f2 w = pk(ex2_approx(-D0), ex2_approx(-D1));
-        num[r] = fma2(w, b[r + 2 + dyi], num[r]);
-        den[r] = add2(den[r], w);
-      }
-    }
-  }
-
-  if (lane == 0 || lane == 31) return;  // halo lanes
-  float *dst = f_override ? f_override : P->f;
-  const float inv_k = 1.0f / k;
-  const int c = tc0 - 2 + 2 * lane;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int gr = tr0 + r;
-    if (gr >= H) break;
-    float n0, n1, d0, d1;
-    up(num[r], n0, n1);
-    up(den[r], d0, d1);
-    if (c < W) dst[(long)gr * W + c] = (n0 / d0) * inv_k;
-    if (c + 1 < W) dst[(long)gr * W + c + 1] = (n1 / d1) * inv_k;
-  }
-}
-
 }  // namespace
 
-// RED_NLM_F32X2=1 selects the packed-FP32 variant (same results, bit for bit).
-static bool nlm_packed() {
-  static const bool on = [] {
-    const char *v = std::getenv("RED_NLM_F32X2");
-    return v != nullptr && v[0] == '1' && v[1] == '\0';
-  }();
-  return on;
+// Work items of one image: a warp tile per band of kNlmR rows and 60 columns.
+void nlm_items(int prob, int H, int W, std::vector<Item> &out) {
+  for (int r0 = 0; r0 < H; r0 += kNlmR)
+    for (int c0 = 0; c0 < W; c0 += kNlmTW) out.push_back({prob, r0, c0, 0});
 }
 
 cudaError_t nlm_prepare(int wy) {
@@ -364,16 +211,10 @@ cudaError_t launch_nlm(const ProbDev *d_probs, const Item *d_items, int n_items,
   const size_t smem = (size_t)wy * (kNlmR + 14) * kStride * sizeof(float);
   dim3 block(32, wy);
   const int ctas = (n_items + wy - 1) / wy;
-  if (nlm_packed()) {
-    if (occ >= 4)
-      k_nlm_x2<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
-    else
-      k_nlm_x2<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
-  } else if (occ >= 4) {
+  if (occ >= 4)
     k_nlm<kNlmR, 4><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
-  } else {
+  else
     k_nlm<kNlmR, 3><<<ctas, block, smem, s>>>(d_probs, d_items, n_items, sa, src_type, f_override);
-  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -53,7 +53,7 @@ red_status guarded(F &&f) {
 
 struct Layout {
   size_t ring, f, spec, kh, cc, gg, row_stats, gram, coef, gamma, state, y, tmp, b0, cx, cr,
-      cp, cap, cz, psf, obj, total;
+      cp, cap, cz, psf, obj, sd, total;
 };
 
 // Work-item lists of one launch group (one problem, or a batch) for one launch shape.
@@ -63,6 +63,7 @@ struct Plan {
   int *d_sr = nullptr;
   int *d_fused = nullptr;     // deblurring problems solved by the cluster kernel
   int n_fused = 0, fused_ncta = 0, fused_tw_m = 0, fused_tw_h = 0, fused_a = 0, fused_buf = 0;
+  int fused_cg = 0;           // C/G values staged per CTA (0: read from global memory)
   int n_nlm = 0, n_rows = 0, n_cols = 0, n_chunks = 0, n_sr = 0;
   int off_nlm = 0, off_rows = 0, off_cols = 0, off_chunks = 0;
   int row_tw_cap = 0, row_buf_cap = 0, col_tw_cap = 0, col_buf_cap = 0;
@@ -78,12 +79,14 @@ struct Plan {
 };
 
 // One operation of the cycle of Algorithm 3: an FP step src -> dst (kind 0) or an
-// extrapolation from `slots` into `out` (kind 1).
+// extrapolation from `slots` into `out` (kind 1). skip_frozen: the step, or the Gram and
+// gamma solve of the extrapolation, is skipped by problems whose gamma is frozen.
 struct CycleOp {
   int kind;
   int src, dst;
   std::vector<int> slots;
   int out;
+  int skip_frozen;
 };
 
 void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src_type,
@@ -91,7 +94,7 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
 void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs &va,
                cudaStream_t s);
 void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaStream_t s);
-std::vector<CycleOp> cycle_ops(int ve, int k, int m);
+std::vector<CycleOp> cycle_ops(int ve, int k, int m, int freeze);
 void prepare_launch_attrs(const Plan &pl);
 int fft_cluster_override();   // RED_FFT_CLUSTER, or -1 when unset
 int sr_cluster_override();    // RED_SR_CLUSTER (8 or 16), or -1 when unset
@@ -114,12 +117,13 @@ struct red_problem_s {
   red_batch_s *own_batch = nullptr;
   std::vector<float> psf_pad;   // host source of the PSF-spectrum upload (kept alive)
   bool khat_ready = false;
+  bool sd_ready = false;        // SD step size computed (it depends on the PSF only)
   ~red_problem_s();
 };
 
 struct red_batch_s {
   std::vector<red_problem_s *> probs;
-  int ve = 0, k = 1, m = 0;
+  int ve = 0, k = 1, m = 0, freeze = 0;
   std::vector<red::ProbDev> pds;
   red::ProbDev *d_pds = nullptr;
   red::ProbState *d_states = nullptr;

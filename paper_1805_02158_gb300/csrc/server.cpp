@@ -71,7 +71,8 @@ std::string key_of(const red_config &c, const std::vector<float> &psf) {
   o << std::setprecision(17);
   o << c.task << "|" << c.height << "x" << c.width << "|" << c.scale << "|" << c.psf_h << "x"
     << c.psf_w << "|" << c.sigma << "|" << c.alpha << "|" << c.nlm_h << "|" << c.ve << "|"
-    << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|" << std::hex;
+    << c.ve_k << "|" << c.ve_m << "|" << c.cg_iters << "|" << c.storage << "|" << c.baseline
+    << "|" << c.sd_mu << "|" << c.ve_freeze << "|" << std::hex;
   for (float v : psf) {
     uint32_t u;
     std::memcpy(&u, &v, 4);
@@ -86,7 +87,8 @@ std::string group_of(const red_config &c) {
   const long n = (long)c.height * c.width;
   const int size_class = n <= 256L * 256 ? 0 : (n <= 512L * 512 ? 1 : 2);
   std::ostringstream o;
-  o << c.task << "|" << size_class << "|" << c.ve << "|" << c.ve_k << "|" << c.ve_m;
+  o << c.task << "|" << size_class << "|" << c.ve << "|" << c.ve_k << "|" << c.ve_m << "|"
+    << c.ve_freeze;
   return o.str();
 }
 
@@ -110,7 +112,7 @@ struct red_server_s {
   std::map<std::string, size_t> pool_bytes;
   std::vector<std::shared_ptr<Request>> running;
   struct Group {                                         // requests sharing launches
-    int ve = 0, k = 1, m = 0;
+    int ve = 0, k = 1, m = 0, freeze = 0;
     std::vector<red_problem_s *> members;                // as of the last table build
     red::Plan plan;
     std::vector<red::ProbDev> pds;
@@ -260,9 +262,9 @@ void launch_group_cycle(red_server_s::Group &g, std::vector<std::shared_ptr<Requ
     prepare_launch_attrs(g.plan);
     g.members = probs;
   }
-  for (const CycleOp &op : cycle_ops(g.ve, g.k, g.m)) {
+  for (const CycleOp &op : cycle_ops(g.ve, g.k, g.m, g.freeze)) {
     if (op.kind == 0) {
-      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1};
+      StepArgs sa{op.src, op.dst, nullptr, nullptr, 1, op.skip_frozen};
       launch_fp_step(g.d_pds, g.plan, sa, 0, s);
     } else {
       VeArgs va{};
@@ -270,6 +272,7 @@ void launch_group_cycle(red_server_s::Group &g, std::vector<std::shared_ptr<Requ
       va.nvec = (int)op.slots.size();
       va.out_slot = op.out;
       va.update_state = 1;
+      va.skip_frozen = op.skip_frozen;
       launch_ve(g.d_pds, n, g.plan, va, s);
     }
   }
@@ -339,6 +342,7 @@ red_server_s::Group &group_for(red_server_s *S, const Request &r) {
     g->ve = r.cfg.ve;
     g->k = r.cfg.ve_k;
     g->m = r.cfg.ve_m;
+    g->freeze = r.cfg.ve_freeze;
     CUDA_OK(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     CUDA_OK(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
   }

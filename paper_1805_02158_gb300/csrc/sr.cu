@@ -352,6 +352,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   const int ncta = cl.num_blocks();
   const ProbDev *P = probs + sr_list[blockIdx.x / ncta];
   if (sa.update_state && P->st->done) return;   // uniform over the cluster
+  if (sa.skip_frozen && P->st->frozen) return;
   const int tid = threadIdx.x;
 
   SrBand g;
@@ -510,16 +511,26 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
     ps[l] = rv;
     dot = fmaf(rv, rv, dot);
   });
-  float rr = cluster_total(cl, slot_b, dot, ncta);
-  if (resident) {
-    fill_halo(rh, rs);
+  // Steepest-descent baseline (SD-MPE, Sec. IV): the step x - mu grad E(x) of Eq. (5) is
+  // x + mu r with r = b0 + alpha f - A x the residual just formed; no CG iterations.
+  const bool sd_step = P->baseline == kBaseSD;   // uniform over the cluster
+  if (sd_step) {
+    const float mu = P->sd->mu_f;
+    __syncthreads();
+    for (int l = tid; l < nl; l += kSrThreads) xs[l] = fmaf(mu, rs[l], xs[l]);
+  }
+  float rr = sd_step ? 0.f : cluster_total(cl, slot_b, dot, ncta);
+  if (!sd_step) {
+    if (resident) {
+      fill_halo(rh, rs);
+      __syncthreads();
+    }
+    band_sb<KH, KW, S>(g, r_row, 0.f, false);   // z = S B p, p = r
     __syncthreads();
   }
-  band_sb<KH, KW, S>(g, r_row, 0.f, false);   // z = S B p, p = r
-  __syncthreads();
 
   float beta = 0.f;   // p = r + beta p is applied in the adjoint pass (p = r at first)
-  for (int it = 0; it < P->cg_iters; ++it) {
+  for (int it = 0; it < (sd_step ? 0 : P->cg_iters); ++it) {
     if (rr == 0.f) break;
     dot = 0.f;
     band_adjoint<KH, KW, S>(g, [&](long e, int l, float acc) {

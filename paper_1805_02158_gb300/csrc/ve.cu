@@ -21,6 +21,12 @@
 //                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
 // Chunks are fixed per problem, so the reduction order (and the result) does not depend
 // on the launch shape or on other problems in the batch.
+//
+// Cycling with frozen gamma (a remark of Sec. III-C): with ProbDev::ve_freeze = n > 0, the
+// n-th successful gamma solve sets the problem's `frozen` flag; from then on the Gram and
+// the solve skip the problem (VeArgs::skip_frozen), its xi stays in ve_coef, and every
+// cycle's combine applies it to x_m .. x_{m+kappa} (the combine never reads x_{m+kappa+1}
+// unless the extrapolation broke down, which a frozen gamma cannot).
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -91,6 +97,7 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
+  if (va.skip_frozen && P->st->frozen) return;
   const int N = P->N;
   const int begin = it.a * kGramChunk;
   const int end = min(N, begin + kGramChunk);
@@ -199,6 +206,7 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
+  if (va.skip_frozen && P->st->frozen) return;
   const int K = va.nvec - 1;
   const int NP = K * (K + 1) / 2;
   const int begin = it.a * kGramChunk;
@@ -430,13 +438,20 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   }
   if (lane != 0) return;
   ProbState *st = P->st;
-  if (update_state) st->ve_steps += 1;
+  if (update_state) {
+    st->ve_steps += 1;
+    st->solved = 1;   // this cycle's combine uses a fresh gamma
+  }
   if (!ok) {
     st->ve_status = 1;
     if (update_state) st->ve_breakdowns += 1;
     return;
   }
   st->ve_status = 0;
+  if (update_state) {
+    st->ve_ok += 1;
+    if (P->ve_freeze > 0 && st->ve_ok >= P->ve_freeze) st->frozen = 1;
+  }
   double acc = 0.0, sabs = 0.0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -451,9 +466,11 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(32) k_ve_solve(const ProbDev *__restrict__ probs, int update_state) {
+__global__ void __launch_bounds__(32)
+k_ve_solve(const ProbDev *__restrict__ probs, int update_state, int skip_frozen) {
   const ProbDev *P = probs + blockIdx.x;
   if (update_state && P->st->done) return;
+  if (skip_frozen && P->st->frozen) return;
   ve_solve_k<K>(P, update_state);
 }
 
@@ -469,6 +486,15 @@ k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeA
   const int begin = it.a * kGramChunk;
   const int end = min(P->N, begin + kGramChunk);
   const int brk = P->st->ve_status;
+  if (va.update_state && it.a == 0 && threadIdx.x == 0) {
+    // one thread per problem: a combine without a fresh solve reuses the frozen xi
+    ProbState *st = P->st;
+    if (!st->solved) {
+      st->ve_steps += 1;
+      st->frozen_steps += 1;
+    }
+    st->solved = 0;
+  }
   float xi[kap > 0 ? kap : 1];
 #pragma unroll
   for (int j = 0; j < kap; ++j) xi[j] = (float)P->ve_coef[j];
@@ -608,11 +634,11 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
   M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
 
 cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int update_state,
-                            cudaStream_t s) {
+                            cudaStream_t s, int skip_frozen) {
   if (n_probs <= 0) return cudaSuccess;
   switch (nvec - 1) {
 #define RED_SOLVE_CASE(k) \
-  case k: k_ve_solve<k><<<n_probs, 32, 0, s>>>(d_probs, update_state); break;
+  case k: k_ve_solve<k><<<n_probs, 32, 0, s>>>(d_probs, update_state, skip_frozen); break;
     RED_K_CASES(RED_SOLVE_CASE)
 #undef RED_SOLVE_CASE
     default: return cudaErrorInvalidValue;

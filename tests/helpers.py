@@ -65,3 +65,43 @@ def assert_step_close(x, ref, label="", rel=STEP_REL_L2, max_abs=STEP_MAX_ABS):
     print(msg)
     assert r <= rel and m <= max_abs, msg
     return r, m
+
+
+# How far a solve's result may move under per-step errors of the FP32 path's size: the
+# oracle's own solve with every FP step's output rounded to 20 or 19 significant bits
+# (relative 2^-21 or 2^-20: the measured per-step error of the GPU path in L2 and at its
+# worst pixels) against the exact FP64 solve. Where the extrapolation weights are large
+# (sum |gamma|, Eq. (21)) this distance exceeds the FP32 bars; the GPU must then stay
+# within ENVELOPE_FACTOR times the larger of the two.
+ENVELOPE_FACTOR = 3.0
+
+
+def solve_bars(sensitivity=None, factor=ENVELOPE_FACTOR):
+    """(rel, db, max_abs) bars of a solve: the FP32 bars, or factor x the method's measured
+    sensitivity where that is larger."""
+    if sensitivity is None:
+        return SOLVE_REL_L2, SOLVE_PSNR_DB, SOLVE_MAX_ABS
+    return (max(SOLVE_REL_L2, factor * sensitivity["rel_l2"]),
+            max(SOLVE_PSNR_DB, factor * sensitivity["psnr_db"]),
+            max(SOLVE_MAX_ABS, factor * sensitivity["max_abs"]))
+
+
+def oracle_sensitivity(make_map, x0, x_ref, x_true, method, m, kappa, calls, bits=(20, 19),
+                       **kw):
+    """Largest distance, over the given roundings, of the oracle's solve with every FP
+    output rounded to that many significant bits from its exact solve x_ref (see
+    ENVELOPE_FACTOR)."""
+    import sys
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    if here not in sys.path:
+        sys.path.insert(0, here)
+    from make_full_size_oracle import Rounded
+    from oracle import red as ored
+    worst = None
+    for b in bits:
+        xp, _ = ored.solve(Rounded(make_map(), b), x0, method, m=m, kappa=kappa,
+                           max_calls=calls, **kw)
+        e = solve_errors(xp, x_ref, x_true)
+        worst = e if worst is None else {k: max(worst[k], e[k]) for k in e}
+    return worst

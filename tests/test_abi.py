@@ -72,6 +72,11 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(psf=np.ones((4, 4)) / 16), red.RED_EINVAL),      # even PSF: no centre tap
     (dict(height=8, width=8, psf=synth.uniform_psf(9)), red.RED_EINVAL),   # PSF > image
     (dict(height=4096, width=4096), red.RED_EINVAL),       # above the 2048 side limit
+    (dict(baseline=5), red.RED_EINVAL),                    # no such baseline map
+    (dict(baseline="sd", sd_mu=-1.0), red.RED_EINVAL),     # negative SD step size
+    (dict(ve_freeze=-1), red.RED_EINVAL),
+    (dict(ve="none", ve_freeze=1), red.RED_EINVAL),        # nothing to freeze
+    (dict(ve_k=1, ve_m=0, ve_freeze=1), red.RED_EINVAL),   # a frozen cycle of 0 steps
 ])
 def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
     base = dict(height=64, width=64, psf=synth.uniform_psf(9))
@@ -92,6 +97,56 @@ def test_16_bit_storage_footprints(lib):
         assert lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out)) == red.RED_OK
         sizes[st] = out.value
     assert sizes["bf16"] == sizes["f16"] == sizes["f32"] - 7 * 64 * 64 * 2
+
+
+@pytest.mark.parametrize("kw", [dict(baseline="sd"), dict(baseline="sd", sd_mu=1.5),
+                                dict(ve_freeze=2), dict(baseline="sd", ve="mpe", ve_k=9),
+                                dict(storage="f16", ve_freeze=1, ve_k=2)])
+def test_sd_and_frozen_configs_accepted(lib, kw):
+    cfg = red.make_config(height=64, width=64, psf=synth.uniform_psf(9), **kw)
+    out = ctypes.c_size_t()
+    assert lib.red_problem_footprint(ctypes.byref(cfg), ctypes.byref(out)) == red.RED_OK
+
+
+STRUCT_PROBE = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "red.h"
+#define F(T, f) printf(#T " " #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("red_config sizeof %zu\n", sizeof(red_config));
+  printf("red_stats sizeof %zu\n", sizeof(red_stats));
+  %FIELDS%
+  return 0;
+}
+"""
+
+
+def test_struct_layout_matches_binding(tmp_path):
+    """Every field of red_config and red_stats sits at the same offset in the C header
+    (compiled with gcc) and in the ctypes binding, and the sizes agree."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lines = []
+    for T, cls in (("red_config", red.Config), ("red_stats", red.Stats)):
+        lines += [f"F({T}, {name})" for name, _ in cls._fields_]
+    src = tmp_path / "probe.c"
+    src.write_text(STRUCT_PROBE.replace("%FIELDS%", "\n  ".join(lines)))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line.strip():
+            T, f, v = line.split()
+            got[(T, f)] = int(v)
+    assert got[("red_config", "sizeof")] == ctypes.sizeof(red.Config)
+    assert got[("red_stats", "sizeof")] == ctypes.sizeof(red.Stats)
+    for T, cls in (("red_config", red.Config), ("red_stats", red.Stats)):
+        for name, _ in cls._fields_:
+            assert got[(T, name)] == getattr(cls, name).offset, (T, name)
 
 
 def test_svdmpe_config_accepted(lib):

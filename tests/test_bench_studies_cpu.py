@@ -70,10 +70,15 @@ class FakeRed:
 
         class B:
             def solve(self, x0s, outs, calls, tol):
+                # error 64 / (calls * speed); fixed-point residual 1 / (calls * speed)
                 red.solves += 1
+                stats = []
                 for P, o in zip(Ps, outs):
                     t = red.truth[P.cfg["id"]]
                     o.a = (t + 64.0 / (max(calls, 1) * speed(P.cfg))).astype(np.float32)
+                    stats.append({"rel_change": 1.0 / (max(calls, 1) * speed(P.cfg)),
+                                  "fp_calls": calls})
+                return stats
         return B()
 
 
@@ -98,6 +103,14 @@ def test_ve_vs_fp_study_counts_calls_in_steps_of_five():
     assert mpe["calls_to_fp200_cost"] == [85, 85] and mpe["calls_to_fp200_psnr"] == [85, 85]
     assert rre["calls_to_fp200_cost"] == [170, 170] and rre["cost_reached"] == 2
     assert out["rre_calls_to_fp200_cost_mean"] == 170.0
+    # the residual criterion: plain FP's residual after 200 calls is 1/200, reached at the
+    # same budgets; the traces hold the mean residual at 5, 25, 45, ... calls
+    assert mpe["calls_to_fp200_residual"] == [85, 85] and rre["residual_reached"] == 2
+    assert out["rre_calls_to_fp200_residual_mean"] == 170.0
+    np.testing.assert_allclose(out["fp_residual_every20_calls_mean"],
+                               [1.0 / c for c in range(5, 201, 20)])
+    np.testing.assert_allclose(mpe["residual_every20_calls_mean"],
+                               [1.0 / (2.4 * c) for c in range(5, 201, 20)])
 
 
 def test_m_kappa_sweep_grid_and_best_pair(monkeypatch):
