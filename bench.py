@@ -254,9 +254,15 @@ def stored_oracle():
     return np.load(path), json.load(open(meta))["cases"]
 
 
-def accuracy_vs_oracle(outs, problems, names, arrays):
+ENVELOPE_FACTOR = 3.0   # as in tests/helpers.py
+
+
+def accuracy_vs_oracle(outs, problems, names, arrays, cases=None):
     """Errors of GPU results against the stored oracle solves of the same problems:
-    relative L2, |PSNR difference| (dB) and max abs, per image and worst."""
+    relative L2, |PSNR difference| (dB) and max abs, per image and worst; with the stored
+    cases, also whether each image is within max(FP32 bar, 3 x the oracle's own movement
+    under per-step perturbations of the FP32 path's size) -- the bar at 200 calls, where
+    the extrapolation weights (Eq. (21)) magnify per-step rounding."""
     per = []
     for o, p, name in zip(outs, problems, names):
         if arrays is None or name not in arrays.files:
@@ -265,12 +271,26 @@ def accuracy_vs_oracle(outs, problems, names, arrays):
         ref = arrays[name].astype(np.float64)
         d_psnr = abs(10 * math.log10(255 ** 2 / np.mean((x - p.x_true) ** 2))
                      - 10 * math.log10(255 ** 2 / np.mean((ref - p.x_true) ** 2)))
-        per.append({"image": name, "rel_l2": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
-                    "psnr_db": float(d_psnr), "max_abs": float(np.abs(x - ref).max())})
+        e = {"image": name, "rel_l2": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+             "psnr_db": float(d_psnr), "max_abs": float(np.abs(x - ref).max())}
+        if cases is not None and name in cases:
+            sens = {m: max(r["at_200"][m] for r in cases[name]["sensitivity"].values())
+                    for m in ("rel_l2", "psnr_db", "max_abs")}
+            bars = {"rel_l2": max(1e-3, ENVELOPE_FACTOR * sens["rel_l2"]),
+                    "psnr_db": max(0.01, ENVELOPE_FACTOR * sens["psnr_db"]),
+                    "max_abs": max(0.5, ENVELOPE_FACTOR * sens["max_abs"])}
+            e["oracle_own_movement"] = sens
+            e["within_envelope"] = all(e[m] <= bars[m] for m in bars)
+        per.append(e)
     if not per:
         return None
     worst = {k: max(e[k] for e in per) for k in ("rel_l2", "psnr_db", "max_abs")}
-    return {"images_checked": len(per), "worst": worst, "per_image": per}
+    out = {"images_checked": len(per), "worst": worst, "per_image": per}
+    if all("within_envelope" in e for e in per):
+        out["all_within_envelope"] = all(e["within_envelope"] for e in per)
+        out["worst_oracle_own_movement"] = {
+            k: max(e["oracle_own_movement"][k] for e in per) for k in ("rel_l2", "psnr_db", "max_abs")}
+    return out
 
 
 def cufft_comparison(problems, torch, steps=200, reps=5):
@@ -499,6 +519,8 @@ def secondary_workloads(red, torch, flush, steps=3, warmup=3):
             arrays, _ = stored_oracle()
             acc = accuracy_vs_oracle(outs, probs, [f"sr256_rre_k5_s{i}" for i in range(len(probs))],
                                      arrays)
+            if acc is not None:
+                acc["storage"] = "bf16 iterates, FP32 arithmetic; errors against the FP64 oracle"
             out[name]["error_vs_fp64_oracle"] = acc if acc is not None else "stored oracle missing"
         del B, Ps
     return out
@@ -696,16 +718,20 @@ def main():
     B.set_phase_timing(False)
 
     # the timed solve's results (identical in every step) against the stored FP64 oracle
-    arrays, _ = stored_oracle()
+    arrays, cases = stored_oracle()
     accuracy = None
     if rank == 0:
         accuracy = accuracy_vs_oracle(outs, problems,
-                                      [f"deblur256_rre_k5_s{s}" for s in problem_seeds(rank)], arrays)
+                                      [f"deblur256_rre_k5_s{s}" for s in problem_seeds(rank)],
+                                      arrays, cases)
         if accuracy is not None:
             w = accuracy["worst"]
-            accuracy["within_bars"] = bool(w["rel_l2"] <= 1e-3 and w["psnr_db"] <= 0.01
-                                           and w["max_abs"] <= 0.5)
-            accuracy["bars"] = {"rel_l2": 1e-3, "psnr_db": 0.01, "max_abs": 0.5}
+            accuracy["within_fp32_bars"] = bool(w["rel_l2"] <= 1e-3 and w["psnr_db"] <= 0.01
+                                                and w["max_abs"] <= 0.5)
+            accuracy["fp32_bars"] = {"rel_l2": 1e-3, "psnr_db": 0.01, "max_abs": 0.5}
+            accuracy["note"] = ("200 FP steps with RRE k=5: the oracle itself moves by up to "
+                                "worst_oracle_own_movement when its FP outputs are rounded to "
+                                "19-20 bits; the bar is max(FP32 bar, 3x that) per image")
             accuracy.pop("per_image")
 
     pix = SIDE * SIDE * N_IMAGES
@@ -763,7 +789,7 @@ def main():
                  "GBps": gram_bytes / (np.mean(gram_ms) / 1e3) / 1e9},
         "combine": {"ms": float(np.mean(comb_ms)), "algorithmic_bytes": comb_bytes,
                     "GBps": comb_bytes / (np.mean(comb_ms) / 1e3) / 1e9},
-        "ve_solve": {"ms": float(np.mean(vs_ms))},
+        "ve_solve": {"ms": float(np.mean(vs_ms)), "note": "runs inside the Gram launch"},
         "nlm": {"ms": float(np.mean(nlm_ms))},
         "hbm_peak_GBps": hbm,
     }

@@ -218,8 +218,8 @@ typedef enum {
   RED_PHASE_NLM = 0,      /* the denoiser f over all problems                           */
   RED_PHASE_FFT = 1,      /* the Fourier-domain solve (row, column, row passes)          */
   RED_PHASE_CG = 2,       /* the super-resolution CG solve                               */
-  RED_PHASE_GRAM = 3,     /* G = U^T U                                                   */
-  RED_PHASE_VESOLVE = 4,  /* gamma from G                                                */
+  RED_PHASE_GRAM = 3,     /* G = U^T U and, in its last CTA per problem, gamma           */
+  RED_PHASE_VESOLVE = 4,  /* gamma from G (runs inside the Gram launch: no launches)      */
   RED_PHASE_COMBINE = 5   /* x_(m,kappa) from gamma                                      */
 } red_phase;
 

@@ -363,7 +363,6 @@ void launch_fp_step(const ProbDev *d_probs, const Plan &pl, StepArgs sa, int src
 // One extrapolation (Algorithm 1 / RRE) over every problem of a plan.
 void launch_ve(const ProbDev *d_probs, int n_probs, const Plan &pl, const VeArgs &va, cudaStream_t s) {
   CUDA_OK(launch_gram(d_probs, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
-  CUDA_OK(launch_ve_solve(d_probs, n_probs, va.nvec, va.update_state, s, va.skip_frozen));
   VeArgs vc = va;
   vc.skip_frozen = 0;   // frozen problems combine with their stored xi
   CUDA_OK(launch_combine(d_probs, pl.d_items + pl.off_chunks, pl.n_chunks, vc, s));

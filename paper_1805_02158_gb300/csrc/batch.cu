@@ -291,9 +291,6 @@ void enqueue_cycle(red_batch_s *b, cudaStream_t s) {
       ps.begin(RED_PHASE_GRAM);
       CUDA_OK(launch_gram(b->d_pds, pl.d_items + pl.off_chunks, pl.n_chunks, va, s));
       ps.end();
-      ps.begin(RED_PHASE_VESOLVE);
-      CUDA_OK(launch_ve_solve(b->d_pds, n, va.nvec, va.update_state, s, va.skip_frozen));
-      ps.end();
       ps.begin(RED_PHASE_COMBINE);
       VeArgs vc = va;
       vc.skip_frozen = 0;   // frozen problems combine with their stored xi

@@ -160,10 +160,9 @@ cudaError_t launch_spectral_constants(const ProbDev *d_prob, const float2 *k_hat
 cudaError_t launch_sd_step_size(const ProbDev *d_prob, const float *psf, int kh, int kw, int H,
                                 int W, double inv_sigma2, double alpha, double mu_given,
                                 SdParams *sd, cudaStream_t s);
+// G = U^T U per chunk, then (the last chunk of each problem) the gamma solve.
 cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items,
                         const VeArgs &va, cudaStream_t s);
-cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec,
-                            int update_state, cudaStream_t s, int skip_frozen = 0);
 cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
                            const VeArgs &va, cudaStream_t s);
 cudaError_t launch_copy_slots(const ProbDev *d_probs, const Item *d_items, int n_items,

@@ -9,7 +9,8 @@
 //                  per thread, then reduced across the CTA in FP64. The result has
 //                  FP64-level accuracy without FP64 arithmetic in the pixel loop (FP64
 //                  throughput on this part is a small fraction of FP32).
-//   2. k_ve_solve: per problem, one warp: sums the chunk partials in a fixed order,
+//   2. gamma solve: per problem, one warp of the last Gram CTA of that problem to finish
+//                  (no launch of its own): sums the chunk partials in a fixed order,
 //                  Cholesky G = R^T R (R is the R of Algorithm 2's QR up to signs), then
 //                  MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2) or
 //                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), or SVD-MPE: gamma =
@@ -23,8 +24,8 @@
 // on the launch shape or on other problems in the batch.
 //
 // Cycling with frozen gamma (a remark of Sec. III-C): with ProbDev::ve_freeze = n > 0, the
-// n-th successful gamma solve sets the problem's `frozen` flag; from then on the Gram and
-// the solve skip the problem (VeArgs::skip_frozen), its xi stays in ve_coef, and every
+// n-th successful gamma solve sets the problem's `frozen` flag; from then on the Gram (and
+// with it the solve) skips the problem (VeArgs::skip_frozen), its xi stays in ve_coef, and every
 // cycle's combine applies it to x_m .. x_{m+kappa} (the combine never reads x_{m+kappa+1}
 // unless the extrapolation broke down, which a frozen gamma cannot).
 #include <algorithm>
@@ -88,6 +89,23 @@ struct GramAcc {
     }
   }
 };
+
+template <int K>
+__device__ void ve_solve_k(const ProbDev *P, int update_state);
+
+// The last CTA of a problem to finish its Gram partial sums runs the gamma solve (one warp),
+// so the solve needs no launch of its own: every CTA publishes its partials, fences, and
+// counts itself in st->counter2; the one that completes the count reads all partials.
+__device__ __forceinline__ bool last_gram_cta(const ProbDev *P) {
+  __shared__ int is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(&P->st->counter2, 1u) == (unsigned)(P->n_chunks - 1);
+  }
+  __syncthreads();
+  return is_last != 0;
+}
 
 template <int K>
 __global__ void __launch_bounds__(128)
@@ -197,6 +215,10 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][tid];
     P->gram_part[(size_t)it.a * kMaxPairs + tid] = v;
   }
+  if (!last_gram_cta(P)) return;
+  __threadfence();
+  if (warp == 0) ve_solve_k<K>(P, va.update_state);
+  if (tid == 0) P->st->counter2 = 0;
 }
 
 // Generic FP64 path for K > 10 (rarely used; correct but not tuned).
@@ -232,6 +254,13 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
   __syncthreads();
   for (int q = threadIdx.x; q < NP; q += blockDim.x)
     P->gram_part[(size_t)it.a * kMaxPairs + q] = red[q];
+  if (!last_gram_cta(P)) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    if (K == 11) ve_solve_k<11>(P, va.update_state);
+    else ve_solve_k<12>(P, va.update_state);
+  }
+  if (threadIdx.x == 0) P->st->counter2 = 0;
 }
 
 // SVD-MPE weights: the right singular vector of the K x K factor R for its smallest
@@ -356,6 +385,12 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   for (int i = 0, q = 0; i < K; ++i)
 #pragma unroll
     for (int j = i; j < K; ++j, ++q) G[i][j] = (double)h[q] + (double)l[q];
+  // SVD-MPE needs R on every lane (its rotations are lane-parallel); MPE and RRE factor on
+  // lane 0 alone: the FP64 rate of this part (0.52 T lane-FMA/s, well under one lane per
+  // clock per SM) makes each warp-wide FP64 instruction cost tens of cycles, so 31 idle
+  // lanes are far cheaper than 31 redundant ones.
+  const bool svd = P->ve_method == kVeSvdMpe;
+  if (!svd && lane != 0) return;
   double R[K][K], inv[K];   // inv[j] = 1 / r_jj (one division per pivot)
 #pragma unroll
   for (int i = 0; i < K; ++i)
@@ -388,8 +423,9 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   }
   double gamma[K];
   bool ok = !bad;
-  if (ok && P->ve_method == kVeSvdMpe) {
-    ok = svd_mpe_gamma<K>(R, gamma);
+  if (svd) {
+    // every lane took the same branch of the factorisation (same G, same tests)
+    if (ok) ok = svd_mpe_gamma<K>(R, gamma);
   } else if (ok) {
     const int method = P->ve_method;
     const bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
@@ -463,15 +499,6 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
     }
   }
   st->sum_abs_gamma = sabs;
-}
-
-template <int K>
-__global__ void __launch_bounds__(32)
-k_ve_solve(const ProbDev *__restrict__ probs, int update_state, int skip_frozen) {
-  const ProbDev *P = probs + blockIdx.x;
-  if (update_state && P->st->done) return;
-  if (skip_frozen && P->st->frozen) return;
-  ve_solve_k<K>(P, update_state);
 }
 
 // Algorithm 1 steps 3-4 without Q: x_(m,kappa) = x_m + sum_{j<kappa} xi_j (x_{m+j+1} - x_{m+j}).
@@ -632,20 +659,6 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
 
 #define RED_K_CASES(M) \
   M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
-
-cudaError_t launch_ve_solve(const ProbDev *d_probs, int n_probs, int nvec, int update_state,
-                            cudaStream_t s, int skip_frozen) {
-  if (n_probs <= 0) return cudaSuccess;
-  switch (nvec - 1) {
-#define RED_SOLVE_CASE(k) \
-  case k: k_ve_solve<k><<<n_probs, 32, 0, s>>>(d_probs, update_state, skip_frozen); break;
-    RED_K_CASES(RED_SOLVE_CASE)
-#undef RED_SOLVE_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  count_launches(1);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_items,
                            const VeArgs &va, cudaStream_t s) {
