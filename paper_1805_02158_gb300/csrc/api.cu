@@ -455,7 +455,7 @@ static void fill_prob_dev(red_problem_s *P) {
   d.psf = reinterpret_cast<const float *>(b + L.psf);
   d.sd = reinterpret_cast<SdParams *>(b + L.sd);
   d.row_stats = reinterpret_cast<float2 *>(b + L.row_stats);
-  d.gram_part = reinterpret_cast<double *>(b + L.gram);
+  d.gram_part = reinterpret_cast<float2 *>(b + L.gram);
   d.ve_coef = reinterpret_cast<double *>(b + L.coef);
   d.gamma = reinterpret_cast<double *>(b + L.gamma);
   d.st = reinterpret_cast<ProbState *>(b + L.state);

@@ -92,7 +92,7 @@ struct ProbDev {
   // steepest descent (baseline kBaseSD): the step size, set up on the device
   struct SdParams *sd;
   // extrapolation
-  double *gram_part;      // n_chunks x kMaxPairs
+  float2 *gram_part;      // n_chunks x kMaxPairs double-float (hi, lo) partial sums
   double *ve_coef;        // kMaxK: xi_j of Algorithm 1 step 3 (difference form), + gamma
   double *gamma;          // kMaxK
   ProbState *st;

@@ -6,17 +6,20 @@
 //                  2048 pixels) reads the K + 1 vectors once with 16-byte loads. The
 //                  differences are split exactly (TwoSum: u = s + e), the products are
 //                  exact (TwoProduct with FMA) and accumulated in double-float (hi + lo)
-//                  per thread, then reduced across the CTA in FP64. The result has
-//                  FP64-level accuracy without FP64 arithmetic in the pixel loop (FP64
-//                  throughput on this part is a small fraction of FP32).
+//                  per thread, then reduced across the warp and the CTA in double-float
+//                  (TwoSum on FP32 units) and published as one (hi, lo) pair per entry.
+//                  The result has FP64-level accuracy without FP64 arithmetic in the pixel
+//                  loop or the reductions (FP64 throughput on this part is a small fraction
+//                  of FP32).
 //   2. gamma solve: per problem, one warp of the last Gram CTA of that problem to finish
-//                  (no launch of its own): sums the chunk partials in a fixed order,
-//                  Cholesky G = R^T R (R is the R of Algorithm 2's QR up to signs), then
-//                  MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2) or
-//                  RRE: R^T R d = 1, and gamma = c / sum c (d / sum d), or SVD-MPE: gamma =
-//                  v / sum v with v the right singular vector of R for its smallest
-//                  singular value (one-sided Jacobi on R, lane-parallel), all in FP64,
-//                  with the rank-loss and existence rules of the oracle.
+//                  (no launch of its own): sums the chunk partials in a fixed order (in
+//                  double-float), then in FP64 G = U^T D U (the Cholesky factor of G, R =
+//                  D^{1/2} U, without its square roots; R is the R of Algorithm 2's QR up
+//                  to signs) and MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1
+//                  step 2, solved as G_{kappa-1} c' = -g) or RRE: G d = 1, gamma = c / sum c
+//                  (d / sum d); or SVD-MPE: Cholesky R, gamma = v / sum v with v the right
+//                  singular vector of R for its smallest singular value (one-sided Jacobi on
+//                  R, lane-parallel); with the rank-loss and existence rules of the oracle.
 //   3. k_combine:  Algorithm 1 steps 3-4 evaluated without Q as
 //                  x_(m,kappa) = x_m + U_{kappa-1} xi (= x_m + Q_{kappa-1} R_{kappa-1} xi),
 //                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
@@ -54,6 +57,27 @@ __device__ __forceinline__ const float *vec_ptr(const ProbDev *P, const VeArgs &
 // A 16-bit ring slot (BF16 or FP16 storage).
 __device__ __forceinline__ const void *vec_ptr_16(const ProbDev *P, const VeArgs &va, int i) {
   return static_cast<const char *>(P->ring) + (size_t)va.slots[i] * P->slot_stride * 2;
+}
+
+// s + e = a + b exactly (TwoSum, round to nearest): the double-float adds below.
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
+  const float s = __fadd_rn(h, h2);
+  const float z = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
+  h = s;
+  l = __fadd_rn(__fadd_rn(l, l2), e);
+}
+
+// 1/d by Newton's iteration for the reciprocal, x <- x + x (1 - d x), from an FP32 start:
+// each step doubles the correct bits (24 -> 48 -> 96), so two give FP64 accuracy with four
+// FMAs in place of a full division. Pivots outside FP32's normal range take the division.
+__device__ __forceinline__ double recip_newton(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double x = (double)__frcp_rn((float)d);
+  x = fma(x, fma(-d, x, 1.0), x);
+  x = fma(x, fma(-d, x, 1.0), x);
+  return x;
 }
 
 template <int K>
@@ -111,7 +135,7 @@ template <int K>
 __global__ void __launch_bounds__(128)
 k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
   constexpr int NP = K * (K + 1) / 2;
-  __shared__ double red[4][NP];
+  __shared__ float2 red[4][NP];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
@@ -198,22 +222,15 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
   for (int q = 0; q < NP; ++q) {
     float h = acc.hi[q], l = acc.lo[q];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
-      const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
-      const float s = __fadd_rn(h, h2);
-      const float z = __fsub_rn(s, h);
-      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
-      h = s;
-      l = __fadd_rn(__fadd_rn(l, l2), e);
-    }
-    if (lane == 0) red[warp][q] = (double)h + (double)l;
+    for (int off = 16; off > 0; off >>= 1)
+      df_add(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
+    if (lane == 0) red[warp][q] = make_float2(h, l);
   }
   __syncthreads();
-  if (tid < NP) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][tid];
-    P->gram_part[(size_t)it.a * kMaxPairs + tid] = v;
+  if (tid < NP) {   // partials stay double-float (hi, lo): the solve sums them in FP32 units
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(h, l, red[w][tid].x, red[w][tid].y);
+    P->gram_part[(size_t)it.a * kMaxPairs + tid] = make_float2(h, l);
   }
   if (!last_gram_cta(P)) return;
   __threadfence();
@@ -252,8 +269,10 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
     red[q] = s;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < NP; q += blockDim.x)
-    P->gram_part[(size_t)it.a * kMaxPairs + q] = red[q];
+  for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+    const float hi = __double2float_rn(red[q]);
+    P->gram_part[(size_t)it.a * kMaxPairs + q] = make_float2(hi, __double2float_rn(red[q] - (double)hi));
+  }
   if (!last_gram_cta(P)) return;
   __threadfence();
   if (threadIdx.x < 32) {
@@ -338,47 +357,35 @@ __device__ bool svd_mpe_gamma(const double (&R)[K][K], double (&gamma)[K]) {
 
 // The tiny FP64 solve for gamma, one warp per problem. Lanes sum the chunk partials of
 // each Gram entry in a fixed order (lane-strided, then a fixed xor tree), so every lane
-// holds G; every lane factors G = R^T R and solves for gamma with K-sized register arrays
-// (SVD-MPE spreads its rotations over the lanes); lane 0 writes the results.
+// holds G; lane 0 factors G = U^T D U (MPE, RRE) and solves for gamma with K-sized register
+// arrays, or every lane factors G = R^T R (SVD-MPE, whose rotations are spread over the
+// lanes); lane 0 writes the results.
 template <int K>
 __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   constexpr int NP = K * (K + 1) / 2;
   constexpr int kap = K - 1;
   const int lane = threadIdx.x & 31;
-  // Sums of the chunk partials in double-float (FP32 TwoSum; the partials themselves carry
-  // the double-float accuracy of k_gram): lane-strided over the chunks, all NP partials of
-  // a chunk loaded together, then a fixed xor tree. The FP64 units, a small fraction of the
-  // FP32 ones on this part, are kept for the factorisation.
+  // Sums of the chunk partials (double-float (hi, lo) pairs from the Gram kernel) in
+  // double-float (FP32 TwoSum): lane-strided over the chunks, all NP partials of a chunk
+  // loaded together, then a fixed xor tree. No FP64 instruction touches the partials: the
+  // FP64 rate of this part is a small fraction of FP32's, and 32 lanes of FP64 conversions
+  // cost more than the sums themselves.
   float h[NP], l[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) h[q] = l[q] = 0.f;
   for (int c = lane; c < P->n_chunks; c += 32) {
-    double v[NP];
+    float2 v[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) v[q] = __ldcg(P->gram_part + (size_t)c * kMaxPairs + q);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const float vh = __double2float_rn(v[q]);
-      const float vl = __double2float_rn(v[q] - (double)vh);
-      const float s = __fadd_rn(h[q], vh);
-      const float z = __fsub_rn(s, h[q]);
-      const float e = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, z)), __fsub_rn(vh, z));
-      h[q] = s;
-      l[q] = __fadd_rn(l[q], __fadd_rn(e, vl));
-    }
+    for (int q = 0; q < NP; ++q) df_add(h[q], l[q], v[q].x, v[q].y);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, h[q], off);
-      const float l2 = __shfl_xor_sync(0xffffffffu, l[q], off);
-      const float s = __fadd_rn(h[q], h2);
-      const float z = __fsub_rn(s, h[q]);
-      const float e = __fadd_rn(__fsub_rn(h[q], __fsub_rn(s, z)), __fsub_rn(h2, z));
-      h[q] = s;
-      l[q] = __fadd_rn(__fadd_rn(l[q], l2), e);
-    }
+    for (int q = 0; q < NP; ++q)
+      df_add(h[q], l[q], __shfl_xor_sync(0xffffffffu, h[q], off),
+             __shfl_xor_sync(0xffffffffu, l[q], off));
   }
   double G[K][K];
 #pragma unroll
@@ -391,85 +398,124 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   // lanes are far cheaper than 31 redundant ones.
   const bool svd = P->ve_method == kVeSvdMpe;
   if (!svd && lane != 0) return;
-  double R[K][K], inv[K];   // inv[j] = 1 / r_jj (one division per pivot)
-#pragma unroll
-  for (int i = 0; i < K; ++i)
-#pragma unroll
-    for (int j = 0; j < K; ++j) R[i][j] = 0.0;
-  // Cholesky with rank checks: r_jj^2 <= tol * ||u_j||^2 marks column j dependent
-  bool bad = false, last_bad = false;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (bad || last_bad) continue;
-    double s = G[j][j];
-#pragma unroll
-    for (int i = 0; i < j; ++i) s -= R[i][j] * R[i][j];
-    const double gjj = G[j][j];
-    if (gjj == 0.0 || s <= kRankTol * gjj) {
-      if (j < K - 1) bad = true;
-      else last_bad = true;
-      continue;
-    }
-    const double rjj = sqrt(s);
-    R[j][j] = rjj;
-    inv[j] = 1.0 / rjj;
-#pragma unroll
-    for (int l = j + 1; l < K; ++l) {
-      double t = G[j][l];
-#pragma unroll
-      for (int i = 0; i < j; ++i) t -= R[i][j] * R[i][l];
-      R[j][l] = t * inv[j];
-    }
-  }
   double gamma[K];
-  bool ok = !bad;
+  bool bad = false, last_bad = false;   // rank loss in one of the first kappa columns / the last
+  bool ok;
   if (svd) {
-    // every lane took the same branch of the factorisation (same G, same tests)
-    if (ok) ok = svd_mpe_gamma<K>(R, gamma);
-  } else if (ok) {
+    // Cholesky G = R^T R with rank checks (r_jj^2 <= tol * ||u_j||^2 marks column j
+    // dependent); every lane factors the same G and takes the same branches
+    double R[K][K], inv[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < K; ++b) R[a][b] = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < K; ++jj) {
+      if (bad || last_bad) continue;
+      double sj = G[jj][jj];
+#pragma unroll
+      for (int a = 0; a < jj; ++a) sj -= R[a][jj] * R[a][jj];
+      if (G[jj][jj] == 0.0 || sj <= kRankTol * G[jj][jj]) {
+        if (jj < K - 1) bad = true;
+        else last_bad = true;
+        continue;
+      }
+      R[jj][jj] = sqrt(sj);
+      inv[jj] = 1.0 / R[jj][jj];
+#pragma unroll
+      for (int b = jj + 1; b < K; ++b) {
+        double t = G[jj][b];
+#pragma unroll
+        for (int a = 0; a < jj; ++a) t -= R[a][jj] * R[a][b];
+        R[jj][b] = t * inv[jj];
+      }
+    }
+    ok = !bad && svd_mpe_gamma<K>(R, gamma);
+  } else {
+    // G = U^T D U (U unit upper triangular, D diagonal: the Cholesky factor without its
+    // square roots, R = D^{1/2} U), so the pivots d_j are the r_jj^2 of the rank test and
+    // the solves need only the reciprocals of the pivots
+    double U[K][K], id[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < K; ++b) U[a][b] = 0.0;
+    double dg[K];
+#pragma unroll
+    for (int jj = 0; jj < K; ++jj) {
+      if (bad || last_bad) continue;
+      double dj = G[jj][jj];
+#pragma unroll
+      for (int a = 0; a < jj; ++a) dj -= U[a][jj] * U[a][jj] * dg[a];
+      if (G[jj][jj] == 0.0 || dj <= kRankTol * G[jj][jj]) {
+        if (jj < K - 1) bad = true;
+        else last_bad = true;
+        continue;
+      }
+      dg[jj] = dj;
+      id[jj] = recip_newton(dj);
+#pragma unroll
+      for (int b = jj + 1; b < K; ++b) {
+        double t = G[jj][b];
+#pragma unroll
+        for (int a = 0; a < jj; ++a) t -= U[a][jj] * U[a][b] * dg[a];
+        U[jj][b] = t * id[jj];
+      }
+    }
+    ok = !bad;
     const int method = P->ve_method;
     const bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
-    if (use_mpe) {
-      // Algorithm 1 step 2: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1
-      double c[K];
+    if (ok && use_mpe) {
+      // Algorithm 1 step 2: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1, solved in its
+      // normal-equation form G_{kappa-1} c' = -g (the leading kappa x kappa block of G and
+      // the first kappa entries of its last column; R_{kappa-1}^T times Algorithm 1's
+      // system): U^T z = -g, then U c' = z / d
+      double c[K], z[K];
+#pragma unroll
+      for (int a = 0; a < kap; ++a) {
+        double t = -G[a][kap];
+#pragma unroll
+        for (int b = 0; b < a; ++b) t -= U[b][a] * z[b];
+        z[a] = t;
+      }
       c[kap] = 1.0;
 #pragma unroll
-      for (int i = kap - 1; i >= 0; --i) {
-        double s = -R[i][kap];
+      for (int a = kap - 1; a >= 0; --a) {
+        double t = z[a] * id[a];
 #pragma unroll
-        for (int j = i + 1; j < kap; ++j) s -= R[i][j] * c[j];
-        c[i] = s * inv[i];
+        for (int b = a + 1; b < kap; ++b) t -= U[a][b] * c[b];
+        c[a] = t;
       }
       double sc = 0.0, sa = 0.0;
 #pragma unroll
-      for (int i = 0; i <= kap; ++i) { sc += c[i]; sa += fabs(c[i]); }
+      for (int a = 0; a <= kap; ++a) { sc += c[a]; sa += fabs(c[a]); }
       if (fabs(sc) <= kSumTol * sa) ok = false;
-      const double isc = 1.0 / sc;
+      const double isc = recip_newton(sc);
 #pragma unroll
-      for (int i = 0; i <= kap; ++i) gamma[i] = c[i] * isc;
-    } else {
-      // RRE: R^T z = 1 (forward), R d = z (backward), gamma = d / sum d
-      double z[K], d[K];
+      for (int a = 0; a <= kap; ++a) gamma[a] = c[a] * isc;
+    } else if (ok) {
+      // RRE, Eq. (19): G d = 1 by U^T z = 1, U d = z / D; gamma = d / sum d
+      double z[K], dv[K];
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        double s = 1.0;
+      for (int a = 0; a < K; ++a) {
+        double t = 1.0;
 #pragma unroll
-        for (int j = 0; j < i; ++j) s -= R[j][i] * z[j];
-        z[i] = s * inv[i];
+        for (int b = 0; b < a; ++b) t -= U[b][a] * z[b];
+        z[a] = t;
       }
 #pragma unroll
-      for (int i = K - 1; i >= 0; --i) {
-        double s = z[i];
+      for (int a = K - 1; a >= 0; --a) {
+        double t = z[a] * id[a];
 #pragma unroll
-        for (int j = i + 1; j < K; ++j) s -= R[i][j] * d[j];
-        d[i] = s * inv[i];
+        for (int b = a + 1; b < K; ++b) t -= U[a][b] * dv[b];
+        dv[a] = t;
       }
       double sd = 0.0;
 #pragma unroll
-      for (int i = 0; i < K; ++i) sd += d[i];
-      const double isd = 1.0 / sd;
+      for (int a = 0; a < K; ++a) sd += dv[a];
+      const double isd = recip_newton(sd);
 #pragma unroll
-      for (int i = 0; i < K; ++i) gamma[i] = d[i] * isd;
+      for (int a = 0; a < K; ++a) gamma[a] = dv[a] * isd;
     }
   }
   if (lane != 0) return;
@@ -701,7 +747,7 @@ struct StaticVe {
   float *out;
   long n;
   int n_chunks;       // kGramChunk-pixel chunks of the vectors
-  double *part;       // gridDim.x (Gram launch) rows of kMaxPairs
+  float2 *part;       // gridDim.x (Gram launch) rows of kMaxPairs (hi, lo) partial sums
   int n_part;
   int method;
   double *coef, *gamma;
@@ -713,7 +759,7 @@ struct StaticVe {
 template <int K>
 __global__ void __launch_bounds__(128) k_gram_static(StaticVe a) {
   constexpr int NP = K * (K + 1) / 2;
-  __shared__ double red[4][NP];
+  __shared__ float2 red[4][NP];
   GramAcc<K> acc;
   acc.zero();
   const int tid = threadIdx.x;
@@ -758,22 +804,15 @@ __global__ void __launch_bounds__(128) k_gram_static(StaticVe a) {
   for (int q = 0; q < NP; ++q) {
     float h = acc.hi[q], l = acc.lo[q];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
-      const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
-      const float s = __fadd_rn(h, h2);
-      const float z = __fsub_rn(s, h);
-      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
-      h = s;
-      l = __fadd_rn(__fadd_rn(l, l2), e);
-    }
-    if (lane == 0) red[warp][q] = (double)h + (double)l;
+    for (int off = 16; off > 0; off >>= 1)
+      df_add(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
+    if (lane == 0) red[warp][q] = make_float2(h, l);
   }
   __syncthreads();
   if (tid < NP) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][tid];
-    a.part[(size_t)blockIdx.x * kMaxPairs + tid] = v;
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(h, l, red[w][tid].x, red[w][tid].y);
+    a.part[(size_t)blockIdx.x * kMaxPairs + tid] = make_float2(h, l);
   }
 }
 
@@ -907,7 +946,7 @@ extern "C" red_status red_ve_extrapolate_static(const void *const *xs_dev, int n
     a.n = n;
     a.n_chunks = (int)((n + kGramChunk - 1) / kGramChunk);
     a.n_part = std::min(a.n_chunks, kStaticGramCtas);
-    a.part = scratch;
+    a.part = reinterpret_cast<float2 *>(scratch);
     a.method = method;
     a.coef = scratch + kStaticPartials;
     a.gamma = a.coef + kMaxK;
