@@ -55,7 +55,8 @@ typedef enum { RED_DEBLUR = 0, RED_SR = 1 } red_task;
 typedef enum { RED_VE_NONE = 0, RED_VE_MPE = 1, RED_VE_RRE = 2, RED_VE_SVDMPE = 3 } red_ve;
 
 /* Storage type of images and iterates; arithmetic is always FP32, the extrapolation
- * Gram matrix and gamma solve FP64-accurate. */
+ * Gram matrix exact-product with double-float sums and the gamma solve double-float (MPE,
+ * RRE) or FP64 (SVD-MPE). */
 typedef enum { RED_F32 = 0, RED_BF16 = 1, RED_F16 = 2 } red_dtype;
 
 /* Baseline map that Algorithm 3 cycles (one denoiser call per step, Sec. IV):
@@ -277,7 +278,7 @@ red_status red_problem_footprint(const red_config *cfg, size_t *bytes);
 
 /* Measures the throughput of the arithmetic units the hot path is bound by, in lane
  * operations per second over the whole device: FP32 FMA (the NLM's arithmetic), the
- * ex2.approx special function (its weights), FP64 FMA (the extrapolation solve) and packed
+ * ex2.approx special function (its weights), FP64 FMA (the SVD-MPE solve) and packed
  * FP32 FMA (fma.rn.f32x2, two lane operations per instruction), each by independent
  * dependency chains on every SM (a few ms; synchronises the stream). No counterpart in the
  * paper: it puts measured peaks beside the derived ones of the roofline. */

@@ -1,6 +1,6 @@
 // Throughput microbenchmarks of the arithmetic units the hot path is bound by: FP32 FMA,
 // scalar and packed f32x2 (the NLM's distance and accumulation arithmetic), the EX2
-// special-function unit (its weights) and FP64 FMA (the extrapolation solve). Each thread runs independent
+// special-function unit (its weights) and FP64 FMA (the SVD-MPE solve). Each thread runs independent
 // dependency chains long enough that issue, not latency, limits them (the iteration loop
 // is unrolled so that loop overhead is a few percent of the issue slots); the grid fills
 // every SM. Used by the benchmark to put the derived peaks beside measured ones.

@@ -13,13 +13,14 @@
 //                  of FP32).
 //   2. gamma solve: per problem, one warp of the last Gram CTA of that problem to finish
 //                  (no launch of its own): sums the chunk partials in a fixed order (in
-//                  double-float), then in FP64 G = U^T D U (the Cholesky factor of G, R =
-//                  D^{1/2} U, without its square roots; R is the R of Algorithm 2's QR up
-//                  to signs) and MPE: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1
-//                  step 2, solved as G_{kappa-1} c' = -g) or RRE: G d = 1, gamma = c / sum c
-//                  (d / sum d); or SVD-MPE: Cholesky R, gamma = v / sum v with v the right
-//                  singular vector of R for its smallest singular value (one-sided Jacobi on
-//                  R, lane-parallel); with the rank-loss and existence rules of the oracle.
+//                  double-float), then, for MPE and RRE in double-float arithmetic on FP32
+//                  units, G = U^T D U (the Cholesky factor of G, R = D^{1/2} U, without its
+//                  square roots; R is the R of Algorithm 2's QR up to signs) and MPE:
+//                  R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1 (Algorithm 1 step 2, solved as
+//                  G_{kappa-1} c' = -g) or RRE: G d = 1, gamma = c / sum c (d / sum d); or
+//                  SVD-MPE in FP64: Cholesky R, gamma = v / sum v with v the right singular
+//                  vector of R for its smallest singular value (one-sided Jacobi on R,
+//                  lane-parallel); with the rank-loss and existence rules of the oracle.
 //   3. k_combine:  Algorithm 1 steps 3-4 evaluated without Q as
 //                  x_(m,kappa) = x_m + U_{kappa-1} xi (= x_m + Q_{kappa-1} R_{kappa-1} xi),
 //                  xi_j = 1 - sum_{i<=j} gamma_i; reads K vectors, writes one.
@@ -42,6 +43,13 @@
 namespace red {
 
 namespace {
+
+// Threads per Gram and per combine work unit (one chunk of kGramChunk pixels). The Gram:
+// 8 pixels per thread, one round of 16-byte loads per vector in flight. The combine: 4
+// rounds of one float4 per vector per thread (measured faster than one round with 512
+// threads: 7.8 vs 9.7 us on ten 256^2 problems, k = 5).
+constexpr int kGramThreads = 256;
+constexpr int kCombineThreads = 128;
 
 __device__ __forceinline__ void two_diff(float a, float b, float &s, float &e) {
   s = __fsub_rn(a, b);
@@ -68,17 +76,55 @@ __device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
   l = __fadd_rn(__fadd_rn(l, l2), e);
 }
 
-// 1/d by Newton's iteration for the reciprocal, x <- x + x (1 - d x), from an FP32 start:
-// each step doubles the correct bits (24 -> 48 -> 96), so two give FP64 accuracy with four
-// FMAs in place of a full division. Pivots outside FP32's normal range take the division.
-__device__ __forceinline__ double recip_newton(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  double x = (double)__frcp_rn((float)d);
-  x = fma(x, fma(-d, x, 1.0), x);
-  x = fma(x, fma(-d, x, 1.0), x);
-  return x;
+// Double-word ("double-float") arithmetic on FP32 units for the MPE / RRE solve: a value is
+// h + l with |l| <= ulp(h) / 2, unit roundoff u = 2^-24. The algorithms are those of Joldes,
+// Muller and Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic" (ACM TOMS 44(2), 2017), with their relative error bounds:
+// AccurateDWPlusDW (3u^2 + 13u^3), DWTimesDW3 (4u^2), DWTimesFP3 (2u^2), DWDivDW2
+// (15u^2 + 56u^3); TwoSum is Knuth's, Fast2Sum Dekker's (|a| >= |b| or a = 0). Every
+// operation is an explicitly rounded intrinsic, so no contraction changes them.
+struct Dw {
+  float h, l;
+};
+__device__ __forceinline__ Dw dw_of(float h, float l = 0.f) { return Dw{h, l}; }
+__device__ __forceinline__ Dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return Dw{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
 }
+__device__ __forceinline__ Dw fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return Dw{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ Dw dw_add(Dw x, Dw y) {
+  const Dw s = two_sum(x.h, y.h);
+  const Dw t = two_sum(x.l, y.l);
+  const Dw v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+__device__ __forceinline__ Dw dw_neg(Dw x) { return Dw{-x.h, -x.l}; }
+__device__ __forceinline__ Dw dw_sub(Dw x, Dw y) { return dw_add(x, dw_neg(y)); }
+__device__ __forceinline__ Dw dw_abs(Dw x) { return x.h < 0.f ? dw_neg(x) : x; }
+__device__ __forceinline__ Dw dw_mul(Dw x, Dw y) {
+  const float ch = __fmul_rn(x.h, y.h);
+  const float cl1 = __fmaf_rn(x.h, y.h, -ch);
+  const float tl1 = __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.l));
+  const float cl2 = __fmaf_rn(x.l, y.h, tl1);
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ Dw dw_mul_f(Dw x, float y) {
+  const float ch = __fmul_rn(x.h, y);
+  const float cl1 = __fmaf_rn(x.h, y, -ch);
+  return fast_two_sum(ch, __fmaf_rn(x.l, y, cl1));
+}
+__device__ __forceinline__ Dw dw_div(Dw x, Dw y) {
+  const float th = __fdiv_rn(x.h, y.h);
+  const Dw r = dw_mul_f(y, th);
+  const float d = __fadd_rn(__fsub_rn(x.h, r.h), __fsub_rn(x.l, r.l));
+  return fast_two_sum(th, __fdiv_rn(d, y.h));
+}
+// x - a * b
+__device__ __forceinline__ Dw dw_fnma(Dw a, Dw b, Dw x) { return dw_sub(x, dw_mul(a, b)); }
 
 template <int K>
 struct GramAcc {
@@ -132,10 +178,10 @@ __device__ __forceinline__ bool last_gram_cta(const ProbDev *P) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kGramThreads)
 k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
   constexpr int NP = K * (K + 1) / 2;
-  __shared__ float2 red[4][NP];
+  __shared__ float2 red[kGramThreads / 32][NP];
   const Item it = items[blockIdx.x];
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
@@ -215,8 +261,7 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
       acc.add(x);
     }
   }
-  // warp reduction in double-float (FP32 units, TwoSum), fixed xor order; FP64 only for
-  // the final per-warp value and the sum over the CTA's warps
+  // warp and CTA reductions in double-float (FP32 units, TwoSum), fixed order
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
@@ -355,56 +400,97 @@ __device__ bool svd_mpe_gamma(const double (&R)[K][K], double (&gamma)[K]) {
   return true;
 }
 
-// The tiny FP64 solve for gamma, one warp per problem. Lanes sum the chunk partials of
-// each Gram entry in a fixed order (lane-strided, then a fixed xor tree), so every lane
-// holds G; lane 0 factors G = U^T D U (MPE, RRE) and solves for gamma with K-sized register
-// arrays, or every lane factors G = R^T R (SVD-MPE, whose rotations are spread over the
-// lanes); lane 0 writes the results.
+__device__ __forceinline__ Dw shfl_xor_dw(Dw x, int off) {
+  return Dw{__shfl_xor_sync(0xffffffffu, x.h, off), __shfl_xor_sync(0xffffffffu, x.l, off)};
+}
+__device__ __forceinline__ Dw shfl_up_dw(Dw x, int off) {
+  return Dw{__shfl_up_sync(0xffffffffu, x.h, off), __shfl_up_sync(0xffffffffu, x.l, off)};
+}
+// Sum over the warp by a fixed xor tree; every lane ends with the same value (each step
+// adds the same two operands on both lanes of a pair, and the double-word sum is
+// commutative: its TwoSum error terms are exact).
+__device__ __forceinline__ Dw warp_sum_dw(Dw x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x = dw_add(x, shfl_xor_dw(x, off));
+  return x;
+}
+
+// The tiny solve for gamma, one warp per problem, written as short loops over shared
+// memory: it runs once per cycle on whichever SM finishes the Gram last, with a cold
+// instruction cache, so its cost is set by the instructions it fetches at least as much as
+// by its arithmetic.
+//   1. G: the chunk partials pass through shared memory 32 chunks at a time (lane r loads
+//      chunk r's partials), and lane q sums entry q over the chunks in increasing order
+//      (double-float TwoSum).
+//   2. MPE and RRE, in double-word arithmetic on FP32 units: G = U^T D U by right-looking
+//      LDL^T (column j: pivot d_j, U_jb = A_jb / d_j on lanes b, trailing update
+//      A_ab -= A_ja U_jb on lanes over the pairs a <= b); the pivots d_j are the r_jj^2 of
+//      Algorithm 2's R = D^{1/2} U, so the rank test is the oracle's. Then U^T z = rhs and
+//      U c = z / D by columns over the lanes (MPE: rhs = -g, the first kappa entries of G's
+//      last column, and c_kappa = 1; RRE: rhs = 1), sum c and sum |c| by xor trees, gamma_j =
+//      c_j / sum c on lane j, xi_j = 1 - sum_{i<=j} gamma_i by a lane scan.
+//   3. SVD-MPE: every lane reads G, factors G = R^T R in FP64 and runs the lane-parallel
+//      rotations of svd_mpe_gamma; lane 0 writes the results.
 template <int K>
 __device__ void ve_solve_k(const ProbDev *P, int update_state) {
   constexpr int NP = K * (K + 1) / 2;
   constexpr int kap = K - 1;
+  constexpr int QL = (NP + 31) / 32;   // Gram entries per lane
+  __shared__ float2 tile[32][NP];      // 32 chunks' partials
+  __shared__ Dw A[K][K];               // G's upper triangle, then the trailing updates
+  __shared__ Dw Us[K][K];              // strict upper part of U
+  __shared__ Dw dg[K], z[K];
   const int lane = threadIdx.x & 31;
-  // Sums of the chunk partials (double-float (hi, lo) pairs from the Gram kernel) in
-  // double-float (FP32 TwoSum): lane-strided over the chunks, all NP partials of a chunk
-  // loaded together, then a fixed xor tree. No FP64 instruction touches the partials: the
-  // FP64 rate of this part is a small fraction of FP32's, and 32 lanes of FP64 conversions
-  // cost more than the sums themselves.
-  float h[NP], l[NP];
+  ProbState *st = P->st;
+
+  // 1. G
+  Dw acc[QL];
 #pragma unroll
-  for (int q = 0; q < NP; ++q) h[q] = l[q] = 0.f;
-  for (int c = lane; c < P->n_chunks; c += 32) {
-    float2 v[NP];
+  for (int i = 0; i < QL; ++i) acc[i] = dw_of(0.f);
+  const int nc = P->n_chunks;
+#pragma unroll 1
+  for (int c0 = 0; c0 < nc; c0 += 32) {
+    const int c = c0 + lane;
+    const float2 *src = P->gram_part + (size_t)min(c, nc - 1) * kMaxPairs;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) v[q] = __ldcg(P->gram_part + (size_t)c * kMaxPairs + q);
+    for (int q = 0; q < NP; ++q) tile[lane][q] = c < nc ? __ldcg(src + q) : make_float2(0.f, 0.f);
+    __syncwarp();
+    const int rows = min(32, nc - c0);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) df_add(h[q], l[q], v[q].x, v[q].y);
+    for (int i = 0; i < QL; ++i) {
+      const int q = lane + 32 * i;
+      if (q < NP) {
+#pragma unroll 4
+        for (int r = 0; r < rows; ++r) {
+          const float2 v = tile[r][q];
+          df_add(acc[i].h, acc[i].l, v.x, v.y);
+        }
+      }
+    }
+    __syncwarp();
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int q = 0; q < NP; ++q)
-      df_add(h[q], l[q], __shfl_xor_sync(0xffffffffu, h[q], off),
-             __shfl_xor_sync(0xffffffffu, l[q], off));
+  for (int i = 0; i < QL; ++i) {
+    const int q = lane + 32 * i;
+    if (q < NP) {
+      int r = 0, rem = q;   // q -> (r, r + rem) in the row-major upper triangle
+      while (rem >= K - r) {
+        rem -= K - r;
+        ++r;
+      }
+      A[r][r + rem] = acc[i];
+    }
   }
-  double G[K][K];
+  __syncwarp();
+
+  if (P->ve_method == kVeSvdMpe) {
+    double G[K][K];
 #pragma unroll
-  for (int i = 0, q = 0; i < K; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-    for (int j = i; j < K; ++j, ++q) G[i][j] = (double)h[q] + (double)l[q];
-  // SVD-MPE needs R on every lane (its rotations are lane-parallel); MPE and RRE factor on
-  // lane 0 alone: the FP64 rate of this part (0.52 T lane-FMA/s, well under one lane per
-  // clock per SM) makes each warp-wide FP64 instruction cost tens of cycles, so 31 idle
-  // lanes are far cheaper than 31 redundant ones.
-  const bool svd = P->ve_method == kVeSvdMpe;
-  if (!svd && lane != 0) return;
-  double gamma[K];
-  bool bad = false, last_bad = false;   // rank loss in one of the first kappa columns / the last
-  bool ok;
-  if (svd) {
-    // Cholesky G = R^T R with rank checks (r_jj^2 <= tol * ||u_j||^2 marks column j
-    // dependent); every lane factors the same G and takes the same branches
-    double R[K][K], inv[K];
+      for (int j = i; j < K; ++j) G[i][j] = (double)A[i][j].h + (double)A[i][j].l;
+    double R[K][K], inv[K], gamma[K];
+    bool bad = false, last_bad = false;   // rank loss in one of the first kappa columns / the last
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
@@ -430,127 +516,128 @@ __device__ void ve_solve_k(const ProbDev *P, int update_state) {
         R[jj][b] = t * inv[jj];
       }
     }
-    ok = !bad && svd_mpe_gamma<K>(R, gamma);
-  } else {
-    // G = U^T D U (U unit upper triangular, D diagonal: the Cholesky factor without its
-    // square roots, R = D^{1/2} U), so the pivots d_j are the r_jj^2 of the rank test and
-    // the solves need only the reciprocals of the pivots
-    double U[K][K], id[K];
+    const bool ok = !bad && svd_mpe_gamma<K>(R, gamma);
+    if (lane != 0) return;
+    if (update_state) {
+      st->ve_steps += 1;
+      st->solved = 1;   // this cycle's combine uses a fresh gamma
+    }
+    if (!ok) {
+      st->ve_status = 1;
+      if (update_state) st->ve_breakdowns += 1;
+      return;
+    }
+    st->ve_status = 0;
+    if (update_state) {
+      st->ve_ok += 1;
+      if (P->ve_freeze > 0 && st->ve_ok >= P->ve_freeze) st->frozen = 1;
+    }
+    double run = 0.0, sabs = 0.0;
 #pragma unroll
-    for (int a = 0; a < K; ++a)
-#pragma unroll
-      for (int b = 0; b < K; ++b) U[a][b] = 0.0;
-    double dg[K];
-#pragma unroll
-    for (int jj = 0; jj < K; ++jj) {
-      if (bad || last_bad) continue;
-      double dj = G[jj][jj];
-#pragma unroll
-      for (int a = 0; a < jj; ++a) dj -= U[a][jj] * U[a][jj] * dg[a];
-      if (G[jj][jj] == 0.0 || dj <= kRankTol * G[jj][jj]) {
-        if (jj < K - 1) bad = true;
-        else last_bad = true;
-        continue;
-      }
-      dg[jj] = dj;
-      id[jj] = recip_newton(dj);
-#pragma unroll
-      for (int b = jj + 1; b < K; ++b) {
-        double t = G[jj][b];
-#pragma unroll
-        for (int a = 0; a < jj; ++a) t -= U[a][jj] * U[a][b] * dg[a];
-        U[jj][b] = t * id[jj];
+    for (int j = 0; j < K; ++j) {
+      P->gamma[j] = gamma[j];
+      sabs += fabs(gamma[j]);
+      if (j < kap) {
+        run += gamma[j];
+        P->ve_coef[j] = 1.0 - run;   // xi_j
       }
     }
-    ok = !bad;
-    const int method = P->ve_method;
-    const bool use_mpe = (method == kVeMpe) || (method == kVeRre && last_bad);
-    if (ok && use_mpe) {
-      // Algorithm 1 step 2: R_{kappa-1} c' = -r_{kappa+1}, c_kappa = 1, solved in its
-      // normal-equation form G_{kappa-1} c' = -g (the leading kappa x kappa block of G and
-      // the first kappa entries of its last column; R_{kappa-1}^T times Algorithm 1's
-      // system): U^T z = -g, then U c' = z / d
-      double c[K], z[K];
-#pragma unroll
-      for (int a = 0; a < kap; ++a) {
-        double t = -G[a][kap];
-#pragma unroll
-        for (int b = 0; b < a; ++b) t -= U[b][a] * z[b];
-        z[a] = t;
-      }
-      c[kap] = 1.0;
-#pragma unroll
-      for (int a = kap - 1; a >= 0; --a) {
-        double t = z[a] * id[a];
-#pragma unroll
-        for (int b = a + 1; b < kap; ++b) t -= U[a][b] * c[b];
-        c[a] = t;
-      }
-      double sc = 0.0, sa = 0.0;
-#pragma unroll
-      for (int a = 0; a <= kap; ++a) { sc += c[a]; sa += fabs(c[a]); }
-      if (fabs(sc) <= kSumTol * sa) ok = false;
-      const double isc = recip_newton(sc);
-#pragma unroll
-      for (int a = 0; a <= kap; ++a) gamma[a] = c[a] * isc;
-    } else if (ok) {
-      // RRE, Eq. (19): G d = 1 by U^T z = 1, U d = z / D; gamma = d / sum d
-      double z[K], dv[K];
-#pragma unroll
-      for (int a = 0; a < K; ++a) {
-        double t = 1.0;
-#pragma unroll
-        for (int b = 0; b < a; ++b) t -= U[b][a] * z[b];
-        z[a] = t;
-      }
-#pragma unroll
-      for (int a = K - 1; a >= 0; --a) {
-        double t = z[a] * id[a];
-#pragma unroll
-        for (int b = a + 1; b < K; ++b) t -= U[a][b] * dv[b];
-        dv[a] = t;
-      }
-      double sd = 0.0;
-#pragma unroll
-      for (int a = 0; a < K; ++a) sd += dv[a];
-      const double isd = recip_newton(sd);
-#pragma unroll
-      for (int a = 0; a < K; ++a) gamma[a] = dv[a] * isd;
-    }
-  }
-  if (lane != 0) return;
-  ProbState *st = P->st;
-  if (update_state) {
-    st->ve_steps += 1;
-    st->solved = 1;   // this cycle's combine uses a fresh gamma
-  }
-  if (!ok) {
-    st->ve_status = 1;
-    if (update_state) st->ve_breakdowns += 1;
+    st->sum_abs_gamma = sabs;
     return;
   }
-  st->ve_status = 0;
-  if (update_state) {
-    st->ve_ok += 1;
-    if (P->ve_freeze > 0 && st->ve_ok >= P->ve_freeze) st->frozen = 1;
-  }
-  double acc = 0.0, sabs = 0.0;
-#pragma unroll
+
+  // 2. MPE / RRE
+  const float rank_tol = (float)kRankTol, sum_tol = (float)kSumTol;
+  // lane j keeps G_jj (the rank test's reference) and -G_{j,kappa} (MPE's right-hand side)
+  const float gdiag = lane < K ? A[lane][lane].h : 0.f;
+  const Dw rhs_mpe = lane < kap ? dw_neg(A[lane][kap]) : dw_of(0.f);
+  int fail = -1;   // first column with rank loss
+#pragma unroll 1
   for (int j = 0; j < K; ++j) {
-    P->gamma[j] = gamma[j];
-    sabs += fabs(gamma[j]);
-    if (j < kap) {
-      acc += gamma[j];
-      P->ve_coef[j] = 1.0 - acc;   // xi_j
+    const Dw dj = A[j][j];
+    const float gjj = __shfl_sync(0xffffffffu, gdiag, j);
+    if (gjj == 0.f || dj.h <= rank_tol * gjj) {
+      fail = j;
+      break;
+    }
+    if (lane == 0) dg[j] = dj;
+    if (j + 1 + lane < K) Us[j][j + 1 + lane] = dw_div(A[j][j + 1 + lane], dj);
+    __syncwarp();
+    const int m = K - 1 - j;   // trailing order
+#pragma unroll 1
+    for (int p = lane; p < m * (m + 1) / 2; p += 32) {
+      int r = 0, rem = p;
+      while (rem >= m - r) {
+        rem -= m - r;
+        ++r;
+      }
+      const int a = j + 1 + r, b = a + rem;
+      A[a][b] = dw_fnma(A[j][a], Us[j][b], A[a][b]);
+    }
+    __syncwarp();
+  }
+  const bool last_bad = fail == K - 1;
+  bool ok = fail < 0 || last_bad;
+  const bool use_mpe = (P->ve_method == kVeMpe) || (P->ve_method == kVeRre && last_bad);
+  Dw c = dw_of(0.f);
+  if (ok) {
+    const int n = use_mpe ? kap : K;
+    if (lane < n) z[lane] = use_mpe ? rhs_mpe : dw_of(1.f);
+    __syncwarp();
+#pragma unroll 1
+    for (int a = 0; a < n; ++a) {   // U^T z = rhs (unit lower), by columns
+      const Dw za = z[a];
+      if (lane > a && lane < n) z[lane] = dw_fnma(Us[a][lane], za, z[lane]);
+      __syncwarp();
+    }
+    if (lane < n) z[lane] = dw_div(z[lane], dg[lane]);
+    __syncwarp();
+#pragma unroll 1
+    for (int a = n - 1; a > 0; --a) {   // U c = z / D (unit upper), by columns
+      const Dw ca = z[a];
+      if (lane < a) z[lane] = dw_fnma(Us[lane][a], ca, z[lane]);
+      __syncwarp();
+    }
+    c = lane < n ? z[lane] : ((use_mpe && lane == kap) ? dw_of(1.f) : dw_of(0.f));
+    const Dw ssum = warp_sum_dw(c);
+    const Dw sa = warp_sum_dw(dw_abs(c));
+    // MPE's existence rule (sum c = 0); RRE's sum d = 1^T G^-1 1 > 0 always
+    if (use_mpe && fabsf(ssum.h) <= sum_tol * sa.h) ok = false;
+    c = dw_div(c, ssum);   // gamma_j on lane j (zero on lanes >= K)
+  }
+  if (lane == 0) {
+    if (update_state) {
+      st->ve_steps += 1;
+      st->solved = 1;   // this cycle's combine uses a fresh gamma
+    }
+    st->ve_status = ok ? 0 : 1;
+    if (update_state) {
+      if (!ok) st->ve_breakdowns += 1;
+      else {
+        st->ve_ok += 1;
+        if (P->ve_freeze > 0 && st->ve_ok >= P->ve_freeze) st->frozen = 1;
+      }
     }
   }
-  st->sum_abs_gamma = sabs;
+  if (!ok) return;
+  // xi_j = 1 - sum_{i<=j} gamma_i (inclusive scan over the lanes), sum |gamma|
+  Dw pre = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const Dw t = shfl_up_dw(pre, off);
+    if (lane >= off) pre = dw_add(t, pre);
+  }
+  const Dw sabs = warp_sum_dw(dw_abs(c));
+  const Dw xi = dw_sub(dw_of(1.f), pre);
+  if (lane < K) P->gamma[lane] = (double)c.h + (double)c.l;
+  if (lane < kap) P->ve_coef[lane] = (double)xi.h + (double)xi.l;
+  if (lane == 0) st->sum_abs_gamma = (double)sabs.h + (double)sabs.l;
 }
 
 // Algorithm 1 steps 3-4 without Q: x_(m,kappa) = x_m + sum_{j<kappa} xi_j (x_{m+j+1} - x_{m+j}).
 // On breakdown the output is the last iterate x_{m+kappa+1}.
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kCombineThreads)
 k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs va) {
   constexpr int kap = K - 1;
   const Item it = items[blockIdx.x];
@@ -692,7 +779,7 @@ cudaError_t launch_gram(const ProbDev *d_probs, const Item *d_items, int n_items
   const int K = va.nvec - 1;
   switch (K) {
 #define RED_GRAM_CASE(k) \
-  case k: k_gram<k><<<n_items, 128, 0, s>>>(d_probs, d_items, va); break;
+  case k: k_gram<k><<<n_items, kGramThreads, 0, s>>>(d_probs, d_items, va); break;
     RED_GRAM_CASE(1) RED_GRAM_CASE(2) RED_GRAM_CASE(3) RED_GRAM_CASE(4) RED_GRAM_CASE(5)
     RED_GRAM_CASE(6) RED_GRAM_CASE(7) RED_GRAM_CASE(8) RED_GRAM_CASE(9) RED_GRAM_CASE(10)
 #undef RED_GRAM_CASE
@@ -711,7 +798,7 @@ cudaError_t launch_combine(const ProbDev *d_probs, const Item *d_items, int n_it
   if (n_items <= 0) return cudaSuccess;
   switch (va.nvec - 1) {
 #define RED_COMBINE_CASE(k) \
-  case k: k_combine<k><<<n_items, 128, 0, s>>>(d_probs, d_items, va); break;
+  case k: k_combine<k><<<n_items, kCombineThreads, 0, s>>>(d_probs, d_items, va); break;
     RED_K_CASES(RED_COMBINE_CASE)
 #undef RED_COMBINE_CASE
     default: return cudaErrorInvalidValue;
@@ -816,7 +903,7 @@ __global__ void __launch_bounds__(128) k_gram_static(StaticVe a) {
   }
 }
 
-// The FP64 solve of ve_solve_k on a descriptor that points into the static scratch.
+// The gamma solve of ve_solve_k on a descriptor that points into the static scratch.
 template <int K>
 __global__ void __launch_bounds__(32) k_ve_solve_static(StaticVe a) {
   ProbDev P{};

@@ -1,10 +1,14 @@
 """The allocation-free extrapolation entry point (red_ve_extrapolate_static) against the
 problem-based one (red_ve_extrapolate) on the same device vectors.
 
-Both evaluate the same Gram matrix with exact products and double-float sums, the same
-FP64 solve and the same combine, so gamma agrees to FP64-level rounding of the partial
-sums (rtol 1e-9) and the outputs to a few float32 ulps (max abs <= 1e-4 on [0, 255]
-images). This file is collected last so that the static scratch is exercised after the
+Both evaluate the same Gram matrix with exact products and double-float sums (reduced in
+different orders: a grid-strided fixed-size scratch here, one row per chunk there), the
+same double-word solve and the same combine. Their G then differ in the last double-word
+bits (~2^-48 relative), which the solve maps to gamma with a factor of cond(G); the cases
+below include a deliberately near-singular G (four differences of a map with three
+distinct eigenvalues), so gamma is compared at rtol 1e-8 (GAMMA_RTOL), still far below the
+float32 rounding of the xi that the combine consumes, and the outputs to a few float32 ulps
+(max abs <= 1e-4 on [0, 255] images). This file is collected last so that the static scratch is exercised after the
 other GPU tests have used the device.
 """
 import ctypes
@@ -17,6 +21,8 @@ from oracle import fp as ofp
 from paper_1805_02158_gb300 import red, synth
 
 pytestmark = pytest.mark.gpu
+
+GAMMA_RTOL = 1e-8
 
 
 def torch_cuda():
@@ -42,7 +48,7 @@ def compare(P, xs_dev, method):
     torch.cuda.synchronize()
     assert st == st_ref
     if g_ref is not None:
-        np.testing.assert_allclose(g, g_ref, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(g, g_ref, rtol=GAMMA_RTOL, atol=1e-12)
     assert float((out_st - out_ref).abs().max()) <= 1e-4
 
 
@@ -77,7 +83,7 @@ def test_static_unaligned_ragged_and_many_chunks():
     out = torch.empty(n + 1, device="cuda")[1:]
     st, g = red.ve_extrapolate_static(flat, out, "rre")
     assert st == st_ref == red.RED_OK
-    np.testing.assert_allclose(g, g_ref, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g, g_ref, rtol=GAMMA_RTOL, atol=1e-12)
     assert float((out.view(81, 54) - out_ref).abs().max()) <= 1e-4
 
     # 1152 chunks of 2048: a linear map with 3 distinct eigenvalues; kappa = 3 (x_0 .. x_4,
@@ -97,7 +103,7 @@ def test_static_unaligned_ragged_and_many_chunks():
     out = torch.empty(m, device="cuda")
     st, g = red.ve_extrapolate_static(vs, out, "rre")
     assert st == st_ref == red.RED_OK
-    np.testing.assert_allclose(g, g_ref, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g, g_ref, rtol=GAMMA_RTOL, atol=1e-12)
     assert float((out.view(H, W) - out_ref).abs().max()) <= 1e-4
     fixed = b.double() / (1 - lam.double())
     assert float((out.double() - fixed).abs().max()) <= 1e-3 * float(fixed.abs().max())
