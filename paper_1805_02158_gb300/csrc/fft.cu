@@ -574,8 +574,9 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
 //   cluster barrier; column FFT, X = C + G F, inverse column FFT; each CTA stores its
 //   columns back into the row-band buffer A of the rows' owners (A is touched by nobody
 //   before, so no barrier is needed first)
-//   cluster barrier; rows C2R of the band -> x_{k+1}, statistics; the last CTA to finish
-//   sums the per-CTA statistics and runs the termination test.
+//   cluster barrier; rows C2R of the band -> x_{k+1}, statistics; every CTA stores its
+//   partial statistics into rank 0's shared memory, and after a third cluster barrier rank
+//   0 sums them and runs the termination test.
 // Global traffic per pixel: f (4 B), C and G (~6 B), x_k for the statistics (4 B) and
 // x_{k+1} (4 B); the spectrum never leaves the chip.
 constexpr int kClusterThreads = 256;   // two CTAs per SM fit, so 16-CTA clusters co-reside
@@ -590,7 +591,7 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
                     int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap, int cg_cap) {
   extern __shared__ float2 sm[];
   __shared__ float red_d[kClusterThreads / 32], red_x[kClusterThreads / 32];
-  __shared__ int is_last;
+  __shared__ float2 cl_stats[16];   // on rank 0: every CTA's (sum d^2, sum x^2), by rank
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
@@ -759,31 +760,25 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     red_x[warp] = sx;
   }
   __syncthreads();
-  if (!sa.update_state) return;   // no distributed shared memory is used past barrier 3
-  // per-CTA partials through global memory; the last CTA of the cluster to arrive sums
-  // them in rank order (fixed order, no extra cluster barriers)
+  if (!sa.update_state) return;   // uniform over the cluster (a launch argument)
+  // per-CTA partials into rank 0's shared memory, one cluster barrier (release / acquire at
+  // cluster scope), then rank 0 sums them in rank order: no GPU-scope fence, no atomic
   if (tid == 0) {
     float td = 0.f, tx = 0.f;
     for (int w = 0; w < (nthr >> 5); ++w) {
       td += red_d[w];
       tx += red_x[w];
     }
-    P->row_stats[rank] = make_float2(td, tx);
-    __threadfence();
-    is_last = atomicAdd(&P->st->counter, 1u) == (unsigned)(ncta - 1);
+    cl.map_shared_rank(cl_stats, 0)[rank] = make_float2(td, tx);
   }
-  __syncthreads();
-  if (tid == 0 && is_last) {
-    __threadfence();
+  cl.sync();
+  if (rank == 0 && tid == 0) {
     double tsd = 0.0, tsx = 0.0;
     for (int q = 0; q < ncta; ++q) {
-      const float2 v = __ldcg(&P->row_stats[q]);
-      tsd += (double)v.x;
-      tsx += (double)v.y;
+      tsd += (double)cl_stats[q].x;
+      tsx += (double)cl_stats[q].y;
     }
     finish_step(P->st, tsd, tsx, sa.dst);
-    P->st->counter = 0;
-    __threadfence();
   }
 }
 

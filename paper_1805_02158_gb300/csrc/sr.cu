@@ -345,8 +345,9 @@ __global__ void __launch_bounds__(kSrThreads, MINB)
 k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, StepArgs sa,
           SrCaps caps, int resident) {
   extern __shared__ float sm_sr[];
-  __shared__ int nz_sh, is_last;
+  __shared__ int nz_sh;
   __shared__ float part_d[kSrWarps], part_x[kSrWarps];
+  __shared__ float2 cl_stats[16];   // on rank 0: every CTA's (sum d^2, sum x^2), by rank
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
@@ -608,9 +609,9 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       }
     }
   }
-  if (!sa.update_state) return;
-  // CTA sums (fixed order), then the last CTA of the cluster to arrive sums them in rank
-  // order and runs the termination test
+  if (!sa.update_state) return;   // uniform over the cluster (a launch argument)
+  // CTA sums (fixed order) into rank 0's shared memory; after a cluster barrier rank 0 sums
+  // them in rank order and runs the termination test (no GPU-scope fence, no atomic)
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -628,18 +629,14 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       td += part_d[w];
       tx += part_x[w];
     }
-    P->row_stats[rank] = make_float2(td, tx);
-    __threadfence();
-    is_last = atomicAdd(&P->st->counter, 1u) == (unsigned)(ncta - 1);
+    cl.map_shared_rank(cl_stats, 0)[rank] = make_float2(td, tx);
   }
-  __syncthreads();
-  if (tid == 0 && is_last) {
-    __threadfence();
+  cl.sync();
+  if (rank == 0 && tid == 0) {
     double tsd = 0.0, tsx = 0.0;
     for (int q = 0; q < ncta; ++q) {
-      const float2 v = __ldcg(&P->row_stats[q]);
-      tsd += (double)v.x;
-      tsx += (double)v.y;
+      tsd += (double)cl_stats[q].x;
+      tsx += (double)cl_stats[q].y;
     }
     ProbState *st = P->st;
     const double rel = tsx > 0.0 ? sqrt(tsd / tsx) : (tsd > 0.0 ? INFINITY : 0.0);
@@ -650,8 +647,6 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       st->converged = rel < st->tol ? 1 : 0;
       st->final_slot = sa.dst;
     }
-    st->counter = 0;
-    __threadfence();
   }
 }
 // b0 = B^T S^T y / sigma^2
