@@ -298,17 +298,13 @@ void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStre
     if (sr_smem_bytes(sr_cap, 0) > sr_limit)
       throw Fail{RED_EUNSUPPORTED, "super-resolution image too large for the CG kernel's shared memory"};
     const int sp = sr_cap.spec737;
-    const int act0 = sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, 0), sp, 2);
+    const int act0 = sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, 0), sp);
     if (act0 < 1) throw Fail{RED_EUNSUPPORTED, "the CG kernel's cluster does not fit on this device"};
     // the band's vectors in shared memory when they fit and as many clusters stay resident
     // as the launch needs
     const int smem1 = sr_smem_bytes(sr_cap, 1);
     sr_cap.resident = (smem1 <= sr_limit &&
-                       sr_max_active_clusters(lc.sr_cluster, smem1, sp, 2) >= std::min(n_sr, act0)) ? 1 : 0;
-    // the larger register budget (one CTA per SM) when every cluster still fits at once
-    sr_cap.minb = 2;
-    if (sp && sr_max_active_clusters(lc.sr_cluster, sr_smem_bytes(sr_cap, sr_cap.resident), sp, 1) >= n_sr)
-      sr_cap.minb = 1;
+                       sr_max_active_clusters(lc.sr_cluster, smem1, sp) >= std::min(n_sr, act0)) ? 1 : 0;
   }
   n_fused = (int)fused.size();
   if (n_fused) upload(d_fused, fused_cap, fused);

@@ -182,7 +182,6 @@ struct SrCaps {
   int band_ext = 0;  // pixels of the largest band with kh - 1 halo rows on each side
   int spec737 = 1;   // every problem has a 7x7 PSF and scale 3 (specialised kernel)
   int resident = 0;  // the band's CG vectors are kept in shared memory
-  int minb = 2;      // register budget: 1 or 2 resident CTAs per SM
   int resident_off = 0;   // (set at launch) word offset of the resident vectors
 };
 void sr_caps(int H, int W, int scale, int kh, int kw, int ncta, SrCaps *c);
@@ -209,7 +208,7 @@ int fft_smem_cols(int tw_cap, int buf_cap);
 void count_launches(uint64_t n);
 cudaError_t fft_prepare(int row_tw_cap, int row_buf_cap, int col_tw_cap, int col_buf_cap);
 cudaError_t sr_prepare(int cluster, int smem);
-int sr_max_active_clusters(int cluster, int smem, int spec737, int minb);
+int sr_max_active_clusters(int cluster, int smem, int spec737);
 cudaError_t nlm_prepare(int wy);
 
 // NLM work items of one image (nlm.cu).

@@ -39,7 +39,10 @@ namespace red {
 
 namespace {
 
-constexpr int kSrThreads = 256;
+// 512 threads, one CTA per SM (the 128-register budget): against 256-thread CTAs, the same
+// on nine 256^2 problems (where the SMs are full either way) and 7-9 % more solves/s when
+// serving, whose SR groups are small enough for a 16-CTA cluster to take 16 SMs.
+constexpr int kSrThreads = 512;
 constexpr int kSrWarps = kSrThreads / 32;
 constexpr int kSrMaxCluster = 16;
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -340,8 +343,8 @@ __device__ __forceinline__ void band_adjoint(const SrBand &g, Epi &&epi) {
 // partials | (resident bands only) x and r with kh - 1 halo rows on each side, p, Ap. The caps are maxima over the launch's
 // problems (sr_caps on the host). When the band's vectors do not fit (large images) they
 // stay in global memory and every loop batches its loads.
-template <int KH, int KW, int S, int MINB>
-__global__ void __launch_bounds__(kSrThreads, MINB)
+template <int KH, int KW, int S>
+__global__ void __launch_bounds__(kSrThreads, 1)
 k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, StepArgs sa,
           SrCaps caps, int resident) {
   extern __shared__ float sm_sr[];
@@ -748,11 +751,10 @@ int sr_smem_bytes(const SrCaps &c, int resident) {
 
 using SrKernel = void (*)(const ProbDev *, const int *, StepArgs, SrCaps, int);
 
-// The instantiations: 7x7 taps at scale 3 with the register budget of one or of two CTAs
-// per SM, and any extents.
-static SrKernel sr_kernel(int spec737, int minb) {
-  if (spec737) return minb == 1 ? k_sr_step<7, 7, 3, 1> : k_sr_step<7, 7, 3, 2>;
-  return k_sr_step<0, 0, 0, 2>;
+// The instantiations: 7x7 taps at scale 3, and any extents.
+static SrKernel sr_kernel(int spec737) {
+  if (spec737) return k_sr_step<7, 7, 3>;
+  return k_sr_step<0, 0, 0>;
 }
 
 // The dynamic shared-memory limit of a kernel only ever grows (high-water mark): launches
@@ -762,8 +764,7 @@ cudaError_t sr_prepare(int cluster, int smem) {
   static int high_water = 0;
   static bool non_portable = false;
   std::lock_guard<std::mutex> lk(mu);
-  for (const void *fn : {(const void *)k_sr_step<7, 7, 3, 1>, (const void *)k_sr_step<7, 7, 3, 2>,
-                         (const void *)k_sr_step<0, 0, 0, 2>}) {
+  for (const void *fn : {(const void *)k_sr_step<7, 7, 3>, (const void *)k_sr_step<0, 0, 0>}) {
     cudaError_t e = cudaSuccess;
     if (cluster > 8 && !non_portable)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -776,7 +777,7 @@ cudaError_t sr_prepare(int cluster, int smem) {
   return cudaSuccess;
 }
 
-int sr_max_active_clusters(int cluster, int smem, int spec737, int minb) {
+int sr_max_active_clusters(int cluster, int smem, int spec737) {
   if (sr_prepare(cluster, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -793,7 +794,7 @@ int sr_max_active_clusters(int cluster, int smem, int spec737, int minb) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (const void *)sr_kernel(spec737, minb), &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (const void *)sr_kernel(spec737), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -818,7 +819,7 @@ cudaError_t launch_sr_step(const ProbDev *d_probs, const int *d_sr_probs, int n_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, sr_kernel(caps.spec737, caps.minb), d_probs, d_sr_probs, sa,
+  cudaError_t e = cudaLaunchKernelEx(&cfg, sr_kernel(caps.spec737), d_probs, d_sr_probs, sa,
                                      c, caps.resident);
   count_launches(1);
   return e;
