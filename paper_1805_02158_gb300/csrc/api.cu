@@ -175,11 +175,12 @@ int fft_cluster_override() {
   return (e && *e) ? std::atoi(e) : -1;
 }
 
-// RED_SR_CLUSTER=<n> forces the cluster size of the super-resolution CG solve (8 or 16).
+// RED_SR_CLUSTER=<n> forces the cluster size of the super-resolution CG solve (8, 10, 12
+// or 16).
 int sr_cluster_override() {
   const char *e = std::getenv("RED_SR_CLUSTER");
   const int v = (e && *e) ? std::atoi(e) : -1;
-  return (v == 8 || v == 16) ? v : -1;
+  return (v == 8 || v == 10 || v == 12 || v == 16) ? v : -1;
 }
 
 void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStream_t stream,

@@ -104,7 +104,7 @@ std::string tune_key(const red_batch_s *b) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  key << "v5|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
+  key << "v6|sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount << "|";
   for (size_t i = 0; i < parts.size(); ++i) key << (i ? "," : "") << parts[i];
   std::string k = key.str();
   std::replace(k.begin(), k.end(), ' ', '_');
@@ -220,7 +220,9 @@ LaunchCfg autotune(red_batch_s *b, cudaStream_t s) {
   if (has_sr) {
     float bt = 1e30f;
     LaunchCfg c = best;
-    for (int cl : {8, 16}) {
+    // 8 and 16 CTAs per problem, and the sizes between them: with one CTA per SM a
+    // cluster must fit in one GPC, so which sizes pack best depends on the batch
+    for (int cl : {8, 10, 12, 16}) {
       c.sr_cluster = cl;
       rebuild(c);
       const Plan &pl = b->plan;

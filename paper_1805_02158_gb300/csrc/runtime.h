@@ -97,7 +97,7 @@ void launch_fft_solve(const ProbDev *d_probs, const Plan &pl, StepArgs sa, cudaS
 std::vector<CycleOp> cycle_ops(int ve, int k, int m, int freeze);
 void prepare_launch_attrs(const Plan &pl);
 int fft_cluster_override();   // RED_FFT_CLUSTER, or -1 when unset
-int sr_cluster_override();    // RED_SR_CLUSTER (8 or 16), or -1 when unset
+int sr_cluster_override();    // RED_SR_CLUSTER (8, 10, 12 or 16), or -1 when unset
 
 }  // namespace red
 

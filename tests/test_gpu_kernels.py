@@ -166,10 +166,10 @@ def test_deblur_linear_solve_alone_matches_closed_form():
     assert_step_close(to_host(out), ref, "linear solve alone")
 
 
-@pytest.mark.parametrize("cluster", ["8", "16"])
+@pytest.mark.parametrize("cluster", ["8", "10", "12", "16"])
 @pytest.mark.parametrize("shape", [(48, 48), (96, 96), (54, 72)])
 def test_sr_fp_step_matches_oracle(shape, cluster, monkeypatch):
-    """One x3 SR FP step (NLM + 20 CG iterations), bands of 8 or 16 CTAs."""
+    """One x3 SR FP step (NLM + 20 CG iterations), bands of 8, 10, 12 or 16 CTAs."""
     torch = torch_cuda()
     monkeypatch.setenv("RED_SR_CLUSTER", cluster)
     h, w = shape
@@ -182,7 +182,8 @@ def test_sr_fp_step_matches_oracle(shape, cluster, monkeypatch):
     assert_step_close(to_host(out), ref, f"SR FP step {shape}, cluster {cluster}")
 
 
-@pytest.mark.parametrize("side,cluster", [(256, "8"), (256, "16"), (1024, "16"), (384, "8")])
+@pytest.mark.parametrize("side,cluster", [(256, "8"), (256, "10"), (256, "12"), (256, "16"), (1024, "16"),
+                                          (384, "8")])
 def test_sr_linear_solve_alone_at_full_size(side, cluster, monkeypatch):
     """The CG solve alone at the workload sizes: a constant image is a fixed point of the
     denoiser (f(x) = x), so one FP step from x = c is 20 CG iterations on
