@@ -748,7 +748,7 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
     const float2 t = out.sd_term(e);
     out.put(e, v.x + t.x, -v.y + t.y, pv, sd, sx);
   }
-  // CTA sums (fixed order); the per-CTA partials are summed below by the last CTA to arrive
+  // CTA sums (fixed order); the per-CTA partials are summed below by rank 0
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
