@@ -428,11 +428,14 @@ static void fill_prob_dev(red_problem_s *P) {
   d.ve_freeze = c.ve_freeze;
   d.inv_sigma2 = (float)(1.0 / (c.sigma * c.sigma));
   d.alpha = (float)c.alpha;
+  d.inv_sigma2_d = 1.0 / (c.sigma * c.sigma);
+  d.alpha_d = c.alpha;
   d.nlm_k = (float)std::sqrt(1.4426950408889634074 / (25.0 * c.nlm_h * c.nlm_h));
   char *b = static_cast<char *>(P->block);
   const Layout &L = P->L;
   d.ring = b + L.ring;
   d.f = reinterpret_cast<float *>(b + L.f);
+  d.y = reinterpret_cast<const float *>(b + L.y);
   if (c.task == RED_DEBLUR) {
     d.spec = reinterpret_cast<float2 *>(b + L.spec);
     d.Kh = reinterpret_cast<const float2 *>(b + L.kh);
@@ -510,7 +513,7 @@ void red::problem_precompute(red_problem_s *P, cudaStream_t s) {
                             pl.col_buf_cap, 0, d.spec, 0, s));
     CUDA_OK(launch_spectral_constants(P->d_pd, d.Kh, d.spec, const_cast<float2 *>(d.Cc),
                                       const_cast<float *>(d.Gg), d.H * d.Wh,
-                                      1.0 / (c.sigma * c.sigma), c.alpha,
+                                      d.inv_sigma2_d, d.alpha_d,
                                       1.0 / ((double)d.H * d.W), s, sd ? d.sd : nullptr));
   } else {
     CUDA_OK(launch_sr_rhs(P->d_pd, y, s));

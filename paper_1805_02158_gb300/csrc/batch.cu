@@ -42,6 +42,8 @@ red_batch_s::~red_batch_s() {
   if (graph) cudaGraphExecDestroy(graph);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   plan.release();
+  pre.release();
+  if (d_pre_const) cudaFree(d_pre_const);
   if (d_pds) cudaFree(d_pds);
   if (d_states) cudaFree(d_states);
   if (d_ptrs) cudaFree(d_ptrs);
@@ -541,6 +543,47 @@ red_status red_solve(red_problem p, const void *x0_dev, int max_fp_calls, double
   });
 }
 
+// The set-up that depends on y (Eq. (7): the half spectrum of y, then C and G) for every
+// deblurring problem of the batch in three launches (rows, columns, constants) instead of
+// three per problem; the same arithmetic, item for item, as problem_precompute. The PSF
+// spectrum (and an SD problem's step size) comes from the problem's creation; where one is
+// missing, every problem takes the per-problem set-up. SR problems form b0 on their own.
+static void batch_precompute(red_batch_s *b, cudaStream_t s) {
+  bool ready = true;
+  for (auto *p : b->probs)
+    if (p->cfg.task == RED_DEBLUR &&
+        (!p->khat_ready || (p->cfg.baseline == RED_BASE_SD && !p->sd_ready)))
+      ready = false;
+  if (!ready) {
+    for (auto *p : b->probs) problem_precompute(p, s);
+    return;
+  }
+  if (!b->pre_ready) {
+    LaunchCfg three = b->lc;
+    three.fft_cluster = 0;   // every deblurring problem on the three-pass items
+    b->pre.build(b->pds, three);
+    std::vector<Item> ci;
+    for (int i = 0; i < (int)b->pds.size(); ++i)
+      if (b->pds[i].task == kDeblur)
+        for (int f = 0; f < b->pds[i].H * b->pds[i].Wh; f += 256) ci.push_back({i, f, 0, 0});
+    if (!ci.empty()) {
+      CUDA_OK(cudaMalloc(&b->d_pre_const, ci.size() * sizeof(Item)));
+      CUDA_OK(cudaMemcpy(b->d_pre_const, ci.data(), ci.size() * sizeof(Item), cudaMemcpyHostToDevice));
+    }
+    b->n_pre_const = (int)ci.size();
+    b->pre_ready = true;
+  }
+  const Plan &pl = b->pre;
+  prepare_launch_attrs(pl);
+  CUDA_OK(launch_fft_r2c(b->d_pds, pl.d_items + pl.off_rows, pl.n_rows, pl.row_tw_cap,
+                         pl.row_buf_cap, nullptr, nullptr, kFftSrcY, s));
+  CUDA_OK(launch_fft_cols(b->d_pds, pl.d_items + pl.off_cols, pl.n_cols, pl.col_tw_cap,
+                          pl.col_buf_cap, 0, nullptr, 0, s));
+  CUDA_OK(launch_spectral_constants_items(b->d_pds, b->d_pre_const, b->n_pre_const, s));
+  for (auto *p : b->probs)
+    if (p->cfg.task != RED_DEBLUR) problem_precompute(p, s);
+}
+
 red_status red_batch_solve_host(red_batch b, const float *const *y_host,
                                 const float *const *x0_host, int max_fp_calls, double rel_tol,
                                 float *const *x_out_host, red_stats *stats, void *stream) {
@@ -564,8 +607,7 @@ red_status red_batch_solve_host(red_batch b, const float *const *y_host,
       x0[i] = tmp;
       xo[i] = tmp;
     }
-    if (y_host)
-      for (int i = 0; i < n; ++i) problem_precompute(b->probs[i], s);
+    if (y_host) batch_precompute(b, s);
     red_status st = batch_solve_impl(b, x0.data(), max_fp_calls, rel_tol, xo.data(), stats, s);
     for (int i = 0; i < n; ++i) {
       red_problem_s *p = b->probs[i];

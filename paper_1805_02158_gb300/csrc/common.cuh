@@ -74,9 +74,11 @@ struct ProbDev {
   int baseline;           // Baseline: FP step of Eq. (7) or SD step on Eq. (5)
   int ve_freeze;          // 0, or freeze gamma after this many successful extrapolations
   float inv_sigma2, alpha;
+  double inv_sigma2_d, alpha_d;   // the same in FP64 (the per-problem spectral constants)
   float nlm_k;            // NLM prescale sqrt(log2(e) / (P^2 h^2))
   void *ring;             // nslots * slot_stride elements (float, bf16 or half)
   float *f;               // denoiser output, N
+  const float *y;         // the observation (deblur: H x W; SR: lh x lw)
   float2 *spec;           // H x Wh half spectrum workspace (deblur)
   const float2 *Kh;       // H x Wh: K, the PSF spectrum (for H x in the objective)
   const float2 *Cc;       // H x Wh: conj(K) Y / (sigma^2 D) / (H W)
@@ -198,6 +200,12 @@ int fft_cluster_smem(int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap, int cg_
 // staging is dropped above it, so the 16-CTA clusters of every problem stay resident).
 constexpr int kClusterSmemTwoPerSm = 112 * 1024;
 cudaError_t fft_cluster_prepare(int smem, int ncta);
+// C and G of every deblurring problem listed (one item per 256 frequencies of a problem:
+// {prob, first frequency}), from its K and the half spectrum of y in its spec buffer.
+cudaError_t launch_spectral_constants_items(const ProbDev *d_probs, const Item *d_items,
+                                            int n_items, cudaStream_t s);
+// Flag of launch_fft_r2c's `skip_done` word: transform each problem's observation y.
+constexpr int kFftSrcY = 4;
 int fft_cluster_max_active(int ncta, int smem);
 cudaError_t launch_fft_solve_cluster(const ProbDev *d_probs, const int *d_list, int n, int ncta,
                                      int tw_cap_m, int tw_cap_h, int a_cap, int buf_cap,

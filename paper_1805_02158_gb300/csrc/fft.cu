@@ -385,7 +385,7 @@ k_fft_r2c(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < M; i += nthr) twm[i] = P->tw_m[i];
   for (int i = tid; i <= M; i += nthr) tww[i] = P->tw_w[i];
-  const float *src = src_override ? src_override : P->f;
+  const float *src = src_override ? src_override : ((skip_done & kFftSrcY) ? P->y : P->f);
   // an SD problem's step transforms x_k (its ring slot, any storage type)
   const bool sd_step = is_step && P->baseline == kBaseSD;
   StepOut xin;
@@ -785,11 +785,11 @@ k_fft_solve_cluster(const ProbDev *__restrict__ probs, const int *__restrict__ l
 // FP solve (sd == null): C = conj(K) Y / (sigma^2 D) / (H W), G = alpha / D / (H W) with
 // D = |K|^2 / sigma^2 + alpha. SD step: C_sd = mu conj(K) Y / sigma^2 / (H W),
 // G_sd = (1 - mu alpha - mu |K|^2 / sigma^2) / (H W).
-__global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,
-                                     float2 *Cc, float *Gg, int n, double inv_sigma2,
-                                     double alpha, double inv_hw, const SdParams *sd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void spectral_constant_at(const float2 *__restrict__ khat,
+                                                     const float2 *__restrict__ yhat, float2 *Cc,
+                                                     float *Gg, int i, double inv_sigma2,
+                                                     double alpha, double inv_hw,
+                                                     const SdParams *sd) {
   const double kr = khat[i].x, ki = khat[i].y;
   const double yr = yhat[i].x, yi = yhat[i].y;
   const double k2 = kr * kr + ki * ki;
@@ -806,6 +806,26 @@ __global__ void k_spectral_constants(const float2 *__restrict__ khat, const floa
   }
   Cc[i] = make_float2((float)((kr * yr + ki * yi) * s), (float)((kr * yi - ki * yr) * s));
   Gg[i] = (float)g;
+}
+
+__global__ void k_spectral_constants(const float2 *__restrict__ khat, const float2 *__restrict__ yhat,
+                                     float2 *Cc, float *Gg, int n, double inv_sigma2,
+                                     double alpha, double inv_hw, const SdParams *sd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  spectral_constant_at(khat, yhat, Cc, Gg, i, inv_sigma2, alpha, inv_hw, sd);
+}
+
+// The same for several problems in one launch: item {prob, first frequency}, 256 each.
+__global__ void __launch_bounds__(256)
+k_spectral_constants_items(const ProbDev *__restrict__ probs, const Item *__restrict__ items) {
+  const Item it = items[blockIdx.x];
+  const ProbDev *P = probs + it.prob;
+  const int i = it.a + threadIdx.x;
+  if (i >= P->H * P->Wh) return;
+  spectral_constant_at(P->Kh, P->spec, const_cast<float2 *>(P->Cc), const_cast<float *>(P->Gg), i,
+                       P->inv_sigma2_d, P->alpha_d, 1.0 / ((double)P->H * P->W),
+                       P->baseline == kBaseSD ? P->sd : nullptr);
 }
 
 // max |K(w)|^2 over the half spectrum (rows u < H, columns v <= W/2), K the DFT of the
@@ -994,6 +1014,14 @@ cudaError_t launch_spectral_constants(const ProbDev *, const float2 *k_hat, cons
                                       const SdParams *sd) {
   k_spectral_constants<<<(n + 255) / 256, 256, 0, s>>>(k_hat, y_hat, Cc, Gg, n, inv_sigma2,
                                                        alpha, inv_hw, sd);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectral_constants_items(const ProbDev *d_probs, const Item *d_items,
+                                            int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  k_spectral_constants_items<<<n_items, 256, 0, s>>>(d_probs, d_items);
   count_launches(1);
   return cudaGetLastError();
 }

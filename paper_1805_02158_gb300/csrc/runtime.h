@@ -133,6 +133,12 @@ struct red_batch_s {
   red::Plan plan;
   red::LaunchCfg lc;
   bool ready = false;
+  // observation-dependent set-up of all deblurring problems at once (host-buffer solves):
+  // three-pass Fourier items over every problem, and one constants item per 256 frequencies
+  red::Plan pre;
+  red::Item *d_pre_const = nullptr;
+  int n_pre_const = 0;
+  bool pre_ready = false;
   std::vector<red::CycleOp> ops;
   int fp_per_cycle = 1;
   cudaGraphExec_t graph = nullptr;

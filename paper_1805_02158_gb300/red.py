@@ -342,22 +342,39 @@ class Batch:
         return float(ms.value), int(n.value)
 
     def solve_host(self, y_hosts, x0_hosts, x_out_hosts, max_fp_calls, rel_tol=0.0, stream=None):
-        """Host float32 buffers (numpy arrays or pinned CPU tensors); copies run inside."""
+        """Host float32 buffers (C-contiguous numpy arrays or contiguous CPU tensors, pinned
+        for asynchronous copies), one per problem: y (the observation, LR-sized for SR) or
+        None to keep each problem's current y, x0 and x_out (HR-sized); copies run inside."""
+        import numpy as np
         n = len(self.problems)
 
-        def ptrs(xs):
+        def ptrs(xs, sizes, what):
+            if len(xs) != n:
+                raise ValueError(f"{what}: {len(xs)} buffers for {n} problems")
             out = []
-            for x in xs:
+            for x, want in zip(xs, sizes):
                 if hasattr(x, "data_ptr"):
+                    import torch
+                    if (x.dtype != torch.float32 or not x.is_contiguous() or x.is_cuda
+                            or x.numel() != want):
+                        raise TypeError(f"{what}: expected contiguous float32 CPU tensors of "
+                                        f"{want} elements")
                     out.append(x.data_ptr())
                 else:
+                    if not (isinstance(x, np.ndarray) and x.dtype == np.float32
+                            and x.flags.c_contiguous and x.size == want):
+                        raise TypeError(f"{what}: expected C-contiguous float32 arrays of "
+                                        f"{want} elements")
                     out.append(x.ctypes.data)
             return (ctypes.c_void_p * n)(*out)
 
-        ya = ptrs(y_hosts) if y_hosts is not None else None
+        hr = [P.cfg.height * P.cfg.width for P in self.problems]
+        lr = [(P.cfg.height // P.cfg.scale) * (P.cfg.width // P.cfg.scale) for P in self.problems]
+        ya = ptrs(y_hosts, lr, "y") if y_hosts is not None else None
         stats = (Stats * n)()
-        st = _check(lib().red_batch_solve_host(self.handle, ya, ptrs(x0_hosts), int(max_fp_calls),
-                                               float(rel_tol), ptrs(x_out_hosts), stats,
+        st = _check(lib().red_batch_solve_host(self.handle, ya, ptrs(x0_hosts, hr, "x0"),
+                                               int(max_fp_calls), float(rel_tol),
+                                               ptrs(x_out_hosts, hr, "x_out"), stats,
                                                _stream_ptr(stream)), "red_batch_solve_host",
                     ok=(RED_OK, RED_ENOT_CONVERGED))
         return [s.as_dict() for s in stats]

@@ -167,6 +167,30 @@ def test_batch_host_buffers_match_device_path():
         np.testing.assert_array_equal(to_host(a), b.numpy())
 
 
+
+def test_batch_host_buffers_mixed_tasks_and_baselines_match_device_path():
+    """The host-buffer entry point re-forms the y-dependent constants of all deblurring
+    problems in three launches over the batch (FP and SD problems of different sizes) and
+    the SR problem's b0 on its own; the solves equal those of the device path bit for bit."""
+    import torch
+    probs = [synth.deblur_small(8), synth.make_deblur(9, 48, 72, synth.gaussian_psf(7, 1.6), 2.0),
+             synth.sr_x3(5, 48)]
+    kws = [dict(), dict(baseline="sd"), dict()]
+    Ps = [red.Problem(red.config_for(p, **kw), to_dev(p.y)) for p, kw in zip(probs, kws)]
+    B = red.Batch(Ps)
+    x0s = [to_dev(f32(p.x0)) for p in probs]
+    outs = [torch.empty_like(x) for x in x0s]
+    B.solve(x0s, outs, 11, 0.0)
+    y_h = [torch.from_numpy(p.y32).pin_memory() for p in probs]
+    x0_h = [torch.from_numpy(p.x0_32).pin_memory() for p in probs]
+    out_h = [torch.empty((p.height, p.width), dtype=torch.float32).pin_memory() for p in probs]
+    with pytest.raises(TypeError):   # float64 host buffers are refused, not misread
+        B.solve_host([f32(p.y) for p in probs], x0_h, out_h, 11, 0.0)
+    B.solve_host(y_h, x0_h, out_h, 11, 0.0)
+    for a, b in zip(outs, out_h):
+        np.testing.assert_array_equal(to_host(a), b.numpy())
+
+
 # 16-bit storage bounds for a 10-step 48x48 SR solve: BF16 keeps 8 significant bits (one
 # rounding is up to 0.5 at values in [128, 256)), FP16 11 bits (up to 0.0625 there); the
 # bounds let the rounding of every stored iterate accumulate over the solve.
