@@ -527,6 +527,7 @@ def secondary_workloads(red, torch, flush, steps=3, warmup=3):
 
 
 SERVE_RATE_HZ = 200.0
+SERVE_LIGHT_HZ = 40.0   # a second, lighter stream: latency without most of the queueing
 SERVE_TOL = 1e-4
 SERVE_CAP = 300
 
@@ -540,18 +541,18 @@ def _serving_input(seed):
             "y": np.ascontiguousarray(p.y.astype(np.float32))}
 
 
-def serving_leg(red, n_req, budget_gb=32, slots=32):
-    """Poisson arrivals (200 req/s) of mixed deblurring / x3 SR requests, sides 128-1024,
-    rel-change tolerance 1e-4, cap 300 FP calls, through the serving loop; latency is
-    submission to completion (host result written). RRE k = 5, then plain FP on the same
+def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32):
+    """Poisson arrivals (rate_hz req/s, seed 0) of mixed deblurring / x3 SR requests, sides
+    128-1024, rel-change tolerance 1e-4, cap 300 FP calls, through the serving loop; latency
+    is submission to completion (host result written). RRE k = 5, then plain FP on the same
     stream for comparison; each broken down by task and by image side."""
     import multiprocessing as mp
     from paper_1805_02158_gb300 import synth
     ctx = mp.get_context("spawn")
     with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         reqs = pool.map(_serving_input, range(n_req))
-    arrivals = synth.poisson_arrivals(SERVE_RATE_HZ, n_req, seed=0)
-    out = {"requests": n_req, "rate_hz": SERVE_RATE_HZ, "tol": SERVE_TOL, "cap_fp_calls": SERVE_CAP,
+    arrivals = synth.poisson_arrivals(rate_hz, n_req, seed=0)
+    out = {"requests": n_req, "rate_hz": rate_hz, "tol": SERVE_TOL, "cap_fp_calls": SERVE_CAP,
            "slots": slots, "budget_gb": budget_gb,
            "mix": {"deblur": sum(r["task"] == "deblur" for r in reqs),
                    "sr": sum(r["task"] == "sr" for r in reqs)}}
@@ -622,8 +623,10 @@ def main():
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer (0: none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
-    ap.add_argument("--serve-requests", type=int, default=1000,
-                    help="requests of the serving leg (0: skip it)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving leg at 200 req/s (0: skip serving)")
+    ap.add_argument("--serve-light-requests", type=int, default=300,
+                    help="requests of the second serving leg at 40 req/s (0: skip it)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the SR and uneven-batch workloads")
     args = ap.parse_args()
@@ -825,9 +828,12 @@ def main():
     secondary = None
     if not args.no_secondary and rank == 0:
         secondary = optional(lambda: secondary_workloads(red, torch, flush))
-    serving = None
+    serving = serving_light = None
     if args.serve_requests > 0 and rank == 0:
         serving = optional(lambda: serving_leg(red, args.serve_requests))
+        if args.serve_light_requests > 0:
+            serving_light = optional(lambda: serving_leg(red, args.serve_light_requests,
+                                                         rate_hz=SERVE_LIGHT_HZ))
 
     if rank != 0:
         if dist:
@@ -861,6 +867,7 @@ def main():
         "m_kappa_sweep_sr": sweep,
         "other_workloads": secondary,
         "serving": serving,
+        "serving_light": serving_light,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -207,8 +207,10 @@ red_status red_batch_solve(red_batch b, const void *const *x0_dev, int max_fp_ca
 
 /* As red_batch_solve, but x0 and x_out are HOST float32 images (pinned or pageable);
  * the host-to-device and device-to-host copies run on `stream` inside the call. If
- * y_host is non-null it also uploads each problem's observation y_host[i] and recomputes
- * its constants first (red_set_observation). */
+ * y_host is non-null it also uploads each problem's observation y_host[i] (LR-sized for
+ * SR) and recomputes its constants first, with the same result as red_set_observation;
+ * the deblurring problems' constants (the half spectrum of y, then C and G of Eq. (7)) are
+ * formed for the whole batch in three launches. */
 red_status red_batch_solve_host(red_batch b, const float *const *y_host,
                                 const float *const *x0_host, int max_fp_calls,
                                 double rel_tol, float *const *x_out_host, red_stats *stats,
