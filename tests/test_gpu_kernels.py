@@ -260,6 +260,61 @@ def test_extrapolation_breakdown_reported():
     assert float((out - xs[-1]).abs().max()) == 0.0
 
 
+
+def _integer_history(dep):
+    """Five iterates x_0 .. x_4 on an integer grid (exact in float32, and so their
+    differences and the Gram entries), whose differences u_0 .. u_3 carry one exact linear
+    dependency: "early" u_1 = u_0 (rank loss in the first kappa columns), "last"
+    u_3 = u_0 - u_1 (rank loss in the last column only)."""
+    rng = np.random.default_rng(7)
+    n = 64 * 64
+    u = [rng.integers(-8, 9, n).astype(np.float64) for _ in range(3)]
+    if dep == "early":
+        u = [u[0], u[0].copy(), u[1], u[2]]
+    else:
+        u = [u[0], u[1], u[2], u[0] - u[1]]
+    xs = [rng.integers(50, 150, n).astype(np.float64)]
+    for d in u:
+        xs.append(xs[-1] + d)
+    return [x.astype(np.float32).reshape(64, 64) for x in xs]
+
+
+@pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
+def test_extrapolation_rank_loss_in_an_early_column_is_a_breakdown(method):
+    """A dependent column among the first kappa (Algorithm 2's r_jj = 0) leaves gamma
+    undefined for every method: breakdown, the last iterate returned, as the oracle."""
+    torch = torch_cuda()
+    xs = _integer_history("early")
+    _, g_ref, info = ove.extrapolate([f32(x) for x in xs], method)
+    assert info["breakdown"] and g_ref is None
+    p = deblur_problem(64, 64)
+    P = red.Problem(red.config_for(p, ve=method, ve_k=4), to_dev(p.y))
+    out = torch.empty((64, 64), device="cuda")
+    st, gamma = P.ve_extrapolate([to_dev(x) for x in xs], out)
+    assert st == red.RED_EVE_BREAKDOWN and gamma is None
+    np.testing.assert_array_equal(to_host(out), xs[-1])
+
+
+@pytest.mark.parametrize("method", ["mpe", "rre", "svdmpe"])
+def test_extrapolation_rank_loss_in_the_last_column(method):
+    """u_3 = u_0 - u_1 exactly: MPE (Algorithm 1 uses only R's leading kappa columns and
+    its last column) gives c = (-1, 1, 0, 1), RRE falls back to MPE (Eq. (19) needs all of
+    R), and SVD-MPE takes the null vector of R; all three as the oracle, and the combination
+    sum gamma_i x_i is the exact fixed point of the dependency."""
+    torch = torch_cuda()
+    xs = _integer_history("last")
+    x_ref, g_ref, info = ove.extrapolate([f32(x) for x in xs], method)
+    assert not info["breakdown"] and info["rank_deficient"] == [3]
+    np.testing.assert_allclose(g_ref, [-1.0, 1.0, 0.0, 1.0], atol=1e-9)
+    p = deblur_problem(64, 64)
+    P = red.Problem(red.config_for(p, ve=method, ve_k=4), to_dev(p.y))
+    out = torch.empty((64, 64), device="cuda")
+    st, gamma = P.ve_extrapolate([to_dev(x) for x in xs], out)
+    assert st == red.RED_OK
+    np.testing.assert_allclose(gamma, g_ref, rtol=1e-6, atol=1e-9)
+    assert_step_close(to_host(out), x_ref, f"{method}, rank loss in the last column", rel=1e-6,
+                      max_abs=1e-3)
+
 def test_measured_unit_peaks_are_plausible():
     """The arithmetic-unit microbenchmarks: FP32 FMA near 152 SMs x 128 lanes x clock, the
     special-function unit a fraction of it, FP64 far below FP32 on this part."""
