@@ -435,7 +435,7 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
   for (int i = tid; i < H; i += nthr) twh[i] = P->tw_h[i];
   float2 *spec = spec_override ? spec_override : P->spec;
   const FastDiv dnc(nc > 0 ? nc : 1);
-  copy_batched<4>(H * nc, tid, nthr,
+  copy_batched<8>(H * nc, tid, nthr,
       [&](int idx) {
         int r, c;
         dnc.divmod(idx, r, c);
@@ -457,21 +457,45 @@ k_fft_cols(const ProbDev *__restrict__ probs, const Item *__restrict__ items, in
     return;
   }
   const float inv_hw = 1.0f / ((float)H * (float)P->W);
-  for (int idx = tid; idx < H * nc; idx += nthr) {
-    int r, c;
-    dnc.divmod(idx, r, c);
-    const long g = (long)r * Wh + c0 + c;
-    const float2 fv = F[c * hs + pidx(r)];
-    float2 xv;
-    if (mode == 1) {
-      const float2 cc = P->Cc[g];
-      const float gg = P->Gg[g];
-      xv = make_float2(fmaf(gg, fv.x, cc.x), fmaf(gg, fv.y, cc.y));
-    } else {
-      const float2 kv = cmul(P->Kh[g], fv);
-      xv = make_float2(kv.x * inv_hw, kv.y * inv_hw);
+  // kU constants (C and G, or K) in flight per thread before any is used: one memory
+  // latency per kU elements instead of one per element
+  constexpr int kU = 8;
+  for (int base = tid; base < H * nc; base += kU * nthr) {
+    float2 cv[kU];
+    float gv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = base + u * nthr;
+      gv[u] = 0.f;
+      if (idx < H * nc) {
+        int r, c;
+        dnc.divmod(idx, r, c);
+        const long g = (long)r * Wh + c0 + c;
+        if (mode == 1) {
+          cv[u] = P->Cc[g];
+          gv[u] = P->Gg[g];
+        } else {
+          cv[u] = P->Kh[g];
+        }
+      }
     }
-    F[c * hs + pidx(r)] = cconj(xv);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < H * nc) {
+        int r, c;
+        dnc.divmod(idx, r, c);
+        const float2 fv = F[c * hs + pidx(r)];
+        float2 xv;
+        if (mode == 1) {
+          xv = make_float2(fmaf(gv[u], fv.x, cv[u].x), fmaf(gv[u], fv.y, cv[u].y));
+        } else {
+          const float2 kv = cmul(cv[u], fv);
+          xv = make_float2(kv.x * inv_hw, kv.y * inv_hw);
+        }
+        F[c * hs + pidx(r)] = cconj(xv);
+      }
+    }
   }
   __syncthreads();
   const float2 *X = fft_smem(F, F == b0 ? b1 : b0, H, nc, hs, twh, tid, nthr);
@@ -507,11 +531,28 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   __syncthreads();
   const float2 *spec = P->spec;
   const FastDiv dm(M);
-  for (int idx = tid; idx < nr * M; idx += nthr) {
-    int row, kk;
-    dm.divmod(idx, row, kk);
-    const float2 *xr = spec + (long)(r0 + row) * Wh;
-    b0[row * ss + pidx(kk)] = c2r_pre(xr[kk], xr[M - kk], tww[kk]);
+  for (int base = tid; base < nr * M; base += 4 * nthr) {   // 8 spectrum loads in flight
+    float2 xa[4], xb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < nr * M) {
+        int row, kk;
+        dm.divmod(idx, row, kk);
+        const float2 *xr = spec + (long)(r0 + row) * Wh;
+        xa[u] = xr[kk];
+        xb[u] = xr[M - kk];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < nr * M) {
+        int row, kk;
+        dm.divmod(idx, row, kk);
+        b0[row * ss + pidx(kk)] = c2r_pre(xa[u], xb[u], tww[kk]);
+      }
+    }
   }
   __syncthreads();
   const float2 *Y = fft_smem(b0, b1, M, nr, ss, twm, tid, nthr);
@@ -522,10 +563,24 @@ k_fft_c2r(const ProbDev *__restrict__ probs, const Item *__restrict__ items, int
   for (int row = warp; row < nr; row += nwarps) {
     const long rowbase = (long)(r0 + row) * W;
     float sd = 0.f, sx = 0.f;
-    for (int n = lane; n < M; n += 32) {
-      const float2 v = Y[row * ss + pidx(n)];
-      const float2 t = out.sd_term(rowbase + 2 * n);
-      out.put(rowbase + 2 * n, v.x + t.x, -v.y + t.y, out.prev(rowbase + 2 * n), sd, sx);
+    for (int n0 = lane; n0 < M; n0 += 4 * 32) {   // x_k (and the SD term) loaded 4 at a time
+      float2 pv[4], tv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = n0 + 32 * u;
+        if (n < M) {
+          pv[u] = out.prev(rowbase + 2 * n);
+          tv[u] = out.sd_term(rowbase + 2 * n);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = n0 + 32 * u;
+        if (n < M) {
+          const float2 v = Y[row * ss + pidx(n)];
+          out.put(rowbase + 2 * n, v.x + tv[u].x, -v.y + tv[u].y, pv[u], sd, sx);
+        }
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
