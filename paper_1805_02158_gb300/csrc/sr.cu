@@ -351,6 +351,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   __shared__ int nz_sh;
   __shared__ float part_d[kSrWarps], part_x[kSrWarps];
   __shared__ float2 cl_stats[16];   // on rank 0: every CTA's (sum d^2, sum x^2), by rank
+  __shared__ int band_start[kSrMaxCluster + 1];   // first HR row of every CTA's band, and H
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
   const int ncta = cl.num_blocks();
@@ -382,6 +383,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
   g.zt = zt;
   g.colmap = colmap;
 
+  for (int q = tid; q <= ncta; q += kSrThreads) band_start[q] = (int)((long)q * g.H / ncta);
   for (int i = tid; i < g.kh * g.kw; i += kSrThreads) taps[i] = P->psf[i];
   for (int t = tid; t < g.T; t += kSrThreads) {
     const int R = wrap1(g.r0 - g.c1 + t, g.H);
@@ -492,6 +494,32 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
       }
     }
   };
+  // Inside the CG loop the halo rows of r are pushed instead: each CTA stores the rows of
+  // its band that lie in other CTAs' halos straight into their extended copies (rows of a
+  // band belong to exactly one CTA, so each halo row has one writer); the cluster barrier
+  // of the r.r reduction that follows makes them visible, and no CTA waits on remote loads.
+  // A halo is overwritten only after the p.Ap barrier of the same iteration, which every
+  // CTA reaches after its last read of the previous r.
+  auto push_halo = [&](float *ext, const float *band_local) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int job = warp; job < ncta * 2 * hw; job += kSrWarps) {
+      const int q = job / (2 * hw), hr = job - q * (2 * hw);
+      const int r0q = band_start[q];
+      const int nbq = band_start[q + 1] - r0q;
+      const int t = hr < hw ? hr : nbq + hr;
+      const int R = wrap1(r0q - hw + t, g.H);
+      if (R < g.r0 || R >= g.r0 + g.nb) continue;   // a row of another band
+      const float *src = band_local + (long)(R - g.r0) * g.W;
+      float *dst = cl.map_shared_rank(ext, q) + (long)t * g.W;
+      if ((g.W & 3) == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int c = lane; c < (g.W >> 2); c += 32) d4[c] = s4[c];
+      } else {
+        for (int c = lane; c < g.W; c += 32) dst[c] = src[c];
+      }
+    }
+  };
   auto x_row = [&](int k, int li, int a) -> const float * {
     if (resident) return xh + (long)(zt[k] - a + hw) * g.W;
     return P->cg_x + (long)wrap1(g.s * li - a + g.c1, g.H) * g.W;
@@ -571,13 +599,15 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
         }
       }
     }
+    // the last iteration's r, beta and z = S B p are not used: x_{k+1} is final
+    if (it + 1 == P->cg_iters) break;
+    if (resident) {
+      __syncthreads();          // the band's new r is complete in shared memory
+      push_halo(rh, rs);
+    }
     const float rr_new = cluster_total(cl, slot_b, dot, ncta);
     beta = rr_new / rr;
     rr = rr_new;
-    if (resident) {
-      fill_halo(rh, rs);
-      __syncthreads();
-    }
     band_sb<KH, KW, S>(g, r_row, beta, true);   // z = S B r + beta z = S B p
     __syncthreads();
   }
