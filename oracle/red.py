@@ -18,7 +18,12 @@ Algorithm 3 (Sec. III-C), with these readings of what the paper leaves open:
     computed gamma by Eq. (11), without the QR and the gamma solve (x_{m+kappa+1} is only
     needed to form U for the solve); before that, cycles are full;
   * the baseline map F may be any map of one denoiser call per step: the FP map of
-    Eq. (7) (fp.FPOperator) or the steepest-descent step of SD-MPE (sd.SDOperator).
+    Eq. (7) (fp.FPOperator) or the steepest-descent step of SD-MPE (sd.SDOperator);
+  * VE terminated by its own criterion, then baseline iterations (the "additional
+    iterations ... after terminating the VE" remark of Sec. III-C): with ve_stop_tol > 0,
+    the first FP step whose relative change falls below ve_stop_tol ends extrapolation;
+    that cycle takes no extrapolation (the next start vector is the last FP iterate, as on
+    a breakdown) and every later step is a plain FP step, until tol or the budget.
 """
 from __future__ import annotations
 
@@ -51,16 +56,24 @@ def rel_change(x_new: np.ndarray, x_old: np.ndarray) -> float:
 
 
 def solve(F, x0: np.ndarray, method: str = "none", m: int = 0, kappa: int = 4,
-          max_calls: int = 200, tol: float = 0.0, callback=None, freeze_after=None):
+          max_calls: int = 200, tol: float = 0.0, callback=None, freeze_after=None,
+          ve_stop_tol: float = 0.0):
     """Algorithm 3 around the baseline map F. Returns (x, stats). `callback(calls, x)` is
     called after every baseline step (for convergence studies). `freeze_after`: None for
-    full cycling, else the number of successful full cycles after which gamma is frozen."""
+    full cycling, else the number of successful full cycles after which gamma is frozen.
+    `ve_stop_tol`: extrapolation ends at the first FP step whose relative change is below
+    it, and plain FP steps follow (0: never)."""
+    if ve_stop_tol > 0.0 and freeze_after is not None:
+        raise ValueError("ve_stop_tol and freeze_after do not combine")
     x = np.asarray(x0, dtype=np.float64).copy()
     calls = 0
     stats = {"fp_calls": 0, "ve_steps": 0, "ve_breakdowns": 0, "gammas": [],
-             "sum_abs_gamma": [], "rel_change": None, "frozen_steps": 0}
+             "sum_abs_gamma": [], "rel_change": None, "frozen_steps": 0, "ve_stopped_at": None}
     frozen = None
     while True:
+        if stats["ve_stopped_at"] is not None:
+            method = "none"
+
         # a frozen cycle needs x_m .. x_{m+kappa} only: x_{m+kappa+1} serves the gamma solve
         per_cycle = m + kappa + (1 if frozen is None else 0)
         stored = [x] if (method != "none" and m == 0) else []
@@ -73,10 +86,12 @@ def solve(F, x0: np.ndarray, method: str = "none", m: int = 0, kappa: int = 4,
                 callback(calls, x)
             if method != "none" and i >= m:
                 stored.append(x)
+            if method != "none" and stats["ve_stopped_at"] is None and rc < ve_stop_tol:
+                stats["ve_stopped_at"] = calls
             if rc < tol or calls >= max_calls:
                 stats.update(fp_calls=calls, rel_change=rc)
                 return x, stats
-        if method == "none":
+        if method == "none" or stats["ve_stopped_at"] is not None:
             continue
         if frozen is not None:
             x = combine_direct(stored, frozen)

@@ -145,3 +145,39 @@ def test_rel_change_hand_computed():
         pytest.approx(1.1180339887498949, rel=1e-14)
     x = np.array([[1.0, -2.0], [2.0, 4.0]])
     assert red.rel_change(x, x) == 0.0
+
+
+def test_ve_stop_tol_zero_and_huge_reduce_to_full_cycling_and_plain_fp():
+    """ve_stop_tol = 0 never ends extrapolation (full cycling, bit for bit); a tolerance
+    above every relative change ends it at the first FP step, after which the driver is the
+    plain FP iteration of Eq. (7), bit for bit."""
+    p = small_deblur(3, 20)
+    F = fp.FPOperator(p.y, p.psf, p.y.shape, 1, p.sigma, p.alpha)
+    x_full, st_full = red.solve(F, p.x0, "rre", kappa=4, max_calls=27)
+    x0s, st0 = red.solve(F, p.x0, "rre", kappa=4, max_calls=27, ve_stop_tol=0.0)
+    np.testing.assert_array_equal(x0s, x_full)
+    assert st0["ve_stopped_at"] is None and st0["ve_steps"] == st_full["ve_steps"] == 5
+    x_fp, _ = red.solve(F, p.x0, "none", max_calls=27)
+    x_big, st_big = red.solve(F, p.x0, "mpe", kappa=4, max_calls=27, ve_stop_tol=1e30)
+    np.testing.assert_array_equal(x_big, x_fp)
+    assert st_big["ve_stopped_at"] == 1 and st_big["ve_steps"] == 0
+
+
+def test_ve_stop_tol_hands_over_to_plain_fp_at_the_first_small_change():
+    """Extrapolation ends at the first FP step whose relative change is below ve_stop_tol:
+    the cycles completed before it extrapolated, and every later step is a plain FP step
+    from that step's iterate (no extrapolation at the end of its cycle either)."""
+    p = small_deblur(4, 20)
+    F = fp.FPOperator(p.y, p.psf, p.y.shape, 1, p.sigma, p.alpha)
+    seen = {}
+    x, st = red.solve(F, p.x0, "rre", kappa=4, max_calls=60, ve_stop_tol=2e-3,
+                      callback=lambda c, v: seen.__setitem__(c, v.copy()))
+    s = st["ve_stopped_at"]
+    assert s is not None and 5 < s < 60
+    assert st["ve_steps"] == s // 5
+    assert st["rel_change"] is not None
+    x_tail, _ = red.solve(F, seen[s], "none", max_calls=60 - s)
+    np.testing.assert_array_equal(x, x_tail)
+    # before the stop every cycle's change stayed at or above the threshold
+    _, st_hi = red.solve(F, p.x0, "rre", kappa=4, max_calls=s - 1, ve_stop_tol=2e-3)
+    assert st_hi["ve_stopped_at"] is None
