@@ -556,7 +556,11 @@ def _serving_input(seed):
             "y": np.ascontiguousarray(p.y.astype(np.float32))}
 
 
-def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32):
+SERVE_VARIANTS = (("rre", "rre", 0.0), ("plain_fp", "none", 0.0))
+
+
+def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32,
+                variants=SERVE_VARIANTS):
     """Poisson arrivals (rate_hz req/s, seed 0) of mixed deblurring / x3 SR requests, sides
     128-1024, rel-change tolerance 1e-4, cap 300 FP calls, through the serving loop; latency
     is submission to completion (host result written). RRE k = 5, then plain FP on the same
@@ -571,12 +575,13 @@ def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32):
            "slots": slots, "budget_gb": budget_gb,
            "mix": {"deblur": sum(r["task"] == "deblur" for r in reqs),
                    "sr": sum(r["task"] == "sr" for r in reqs)}}
-    for ve in ("rre", "none"):
+    for key, ve, ve_stop in variants:
         S = red.Server(budget_gb << 30, slots)
         outs = [np.zeros((r["height"], r["width"]), np.float32) for r in reqs]
         cfgs = [red.make_config(task=r["task"], height=r["height"], width=r["width"],
                                 scale=r["scale"], psf=r["psf"], sigma=r["sigma"], alpha=r["alpha"],
-                                nlm_h=r["nlm_h"], ve=ve, ve_k=VE_K) for r in reqs]
+                                nlm_h=r["nlm_h"], ve=ve, ve_k=VE_K, ve_stop_tol=ve_stop)
+                for r in reqs]
         tickets = []
         t0 = time.perf_counter()
         for i, r in enumerate(reqs):
@@ -597,7 +602,7 @@ def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32):
             first_bad = next(st for st in statuses if st not in (red.RED_OK, red.RED_ENOT_CONVERGED))
             print(f"serving: {failed} requests failed ({red.status_string(first_bad)})", file=sys.stderr)
         if not good:
-            out["rre" if ve == "rre" else "plain_fp"] = {"failed": failed}
+            out[key] = {"failed": failed}
             continue
         tasks = [reqs[i]["task"] for i in good]
         sides = [max(reqs[i]["height"], reqs[i]["width"]) for i in good]
@@ -616,7 +621,7 @@ def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32):
                     "fp_calls_mean": float(calls[sel].mean()),
                     "converged_frac": float(conv[sel].mean())}
 
-        out["rre" if ve == "rre" else "plain_fp"] = {
+        out[key] = {
             "failed": failed,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "solves_per_s": n_req / wall, "mpix_iter_per_s": float((pix * calls).sum()) / wall / 1e6,

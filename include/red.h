@@ -92,6 +92,13 @@ typedef struct {
                          /* cycle solves for gamma; n >= 1 = after n successful          */
                          /* extrapolations, later cycles run ve_m + ve_k - 1 steps and   */
                          /* combine with the last gamma (needs ve_m + ve_k >= 2)         */
+  double ve_stop_tol;    /* extrapolation ended by its own criterion, then baseline steps */
+                         /* (the "additional iterations after terminating the VE" remark  */
+                         /* of Sec. III-C): at the first FP step whose relative change is  */
+                         /* below ve_stop_tol, that cycle takes no extrapolation and every */
+                         /* later step is a plain baseline step, until rel_tol or the      */
+                         /* budget; 0 = never (full cycling). Needs ve != RED_VE_NONE and  */
+                         /* ve_freeze = 0                                                  */
 } red_config;
 
 typedef struct {

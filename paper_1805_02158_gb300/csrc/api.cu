@@ -143,6 +143,13 @@ static void validate(const red_config *c) {
     // a frozen cycle runs ve_m + ve_k - 1 baseline steps: at least one
     CHECK_ARG(c->ve_m + c->ve_k >= 2, "ve_freeze needs ve_m + ve_k >= 2");
   }
+  CHECK_ARG(c->ve_stop_tol >= 0.0 && std::isfinite(c->ve_stop_tol),
+            "ve_stop_tol must be finite and >= 0");
+  if (c->ve_stop_tol > 0.0) {
+    CHECK_ARG(c->ve != RED_VE_NONE, "ve_stop_tol needs an extrapolation method");
+    // a frozen cycle has no last iterate to carry on from
+    CHECK_ARG(c->ve_freeze == 0, "ve_stop_tol and ve_freeze do not combine");
+  }
 }
 
 // ---------------------------------------------------------------------------------------

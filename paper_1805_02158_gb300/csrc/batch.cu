@@ -401,6 +401,7 @@ red_status batch_solve_impl(red_batch_s *b, const void *const *x0, int max_calls
     std::memset(&st, 0, sizeof(st));
     st.max_calls = max_calls;
     st.tol = tol;
+    st.ve_stop_tol = b->probs[i]->cfg.ve_stop_tol;
     st.done = max_calls <= 0 ? 1 : 0;
   }
   CUDA_OK(cudaMemcpyAsync(b->d_ptrs, b->h_ptrs, sizeof(float *) * 2 * n, cudaMemcpyHostToDevice, s));

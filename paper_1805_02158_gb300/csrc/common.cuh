@@ -44,6 +44,9 @@ struct ProbState {
   int frozen;          // 1 once ve_ok reached ve_freeze: later cycles reuse xi
   int solved;          // 1 between a gamma solve and the combine that uses it
   int frozen_steps;    // combines with the frozen xi
+  // extrapolation ended by the relative-change criterion (red_config::ve_stop_tol)
+  double ve_stop_tol;  // 0: never
+  int ve_off;          // 1 from the first FP step whose relative change was below it
 };
 
 // Step size of the steepest-descent baseline: mu = 1 / (max |K(w)|^2 / sigma^2 + alpha)

@@ -353,6 +353,7 @@ __device__ __forceinline__ void finish_step(ProbState *st, double sd, double sx,
   const double rel = sx > 0.0 ? sqrt(sd / sx) : (sd > 0.0 ? INFINITY : 0.0);
   st->rel_change = rel;
   st->calls += 1;
+  if (rel < st->ve_stop_tol) st->ve_off = 1;   // extrapolation ends, baseline steps follow
   if (rel < st->tol || st->calls >= st->max_calls) {
     st->done = 1;
     st->converged = rel < st->tol ? 1 : 0;

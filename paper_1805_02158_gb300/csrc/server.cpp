@@ -223,6 +223,7 @@ void admit(red_server_s *S, const std::shared_ptr<Request> &r) {
   ProbState st{};
   st.max_calls = r->max_calls;
   st.tol = r->tol;
+  st.ve_stop_tol = r->cfg.ve_stop_tol;
   st.done = r->max_calls <= 0 ? 1 : 0;
   CUDA_OK(cudaMemcpyAsync(blk + P->L.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   // the x0 host vector must outlive the copy

@@ -675,6 +675,7 @@ k_sr_step(const ProbDev *__restrict__ probs, const int *__restrict__ sr_list, St
     const double rel = tsx > 0.0 ? sqrt(tsd / tsx) : (tsd > 0.0 ? INFINITY : 0.0);
     st->rel_change = rel;
     st->calls += 1;
+    if (rel < st->ve_stop_tol) st->ve_off = 1;   // extrapolation ends, baseline steps follow
     if (rel < st->tol || st->calls >= st->max_calls) {
       st->done = 1;
       st->converged = rel < st->tol ? 1 : 0;

@@ -186,6 +186,7 @@ k_gram(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeArgs
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
   if (va.skip_frozen && P->st->frozen) return;
+  if (va.update_state && P->st->ve_off) return;   // extrapolation has ended for this problem
   const int N = P->N;
   const int begin = it.a * kGramChunk;
   const int end = min(N, begin + kGramChunk);
@@ -291,6 +292,7 @@ k_gram_generic(const ProbDev *__restrict__ probs, const Item *__restrict__ items
   const ProbDev *P = probs + it.prob;
   if (va.update_state && P->st->done) return;
   if (va.skip_frozen && P->st->frozen) return;
+  if (va.update_state && P->st->ve_off) return;   // extrapolation has ended for this problem
   const int K = va.nvec - 1;
   const int NP = K * (K + 1) / 2;
   const int begin = it.a * kGramChunk;
@@ -645,11 +647,14 @@ k_combine(const ProbDev *__restrict__ probs, const Item *__restrict__ items, VeA
   if (va.update_state && P->st->done) return;
   const int begin = it.a * kGramChunk;
   const int end = min(P->N, begin + kGramChunk);
-  const int brk = P->st->ve_status;
+  // the last iterate passes on unchanged after a breakdown, and once extrapolation has
+  // ended (ve_stop_tol): the next cycle's steps are then plain baseline steps
+  const bool ve_off = va.update_state && P->st->ve_off;
+  const int brk = P->st->ve_status || ve_off;
   if (va.update_state && it.a == 0 && threadIdx.x == 0) {
     // one thread per problem: a combine without a fresh solve reuses the frozen xi
     ProbState *st = P->st;
-    if (!st->solved) {
+    if (!st->solved && !ve_off) {
       st->ve_steps += 1;
       st->frozen_steps += 1;
     }

@@ -43,6 +43,7 @@ class Config(ctypes.Structure):
         ("ve", ctypes.c_int), ("ve_k", ctypes.c_int), ("ve_m", ctypes.c_int),
         ("cg_iters", ctypes.c_int), ("storage", ctypes.c_int),
         ("baseline", ctypes.c_int), ("sd_mu", ctypes.c_double), ("ve_freeze", ctypes.c_int),
+        ("ve_stop_tol", ctypes.c_double),
     ]
 
 
@@ -175,8 +176,10 @@ def _dptr(t, shape=None):
 
 def make_config(task="deblur", height=64, width=64, scale=1, psf=None, sigma=2 ** 0.5,
                 alpha=0.02, nlm_h=10.0, ve="rre", ve_k=5, ve_m=0, cg_iters=20,
-                storage="f32", baseline="fp", sd_mu=0.0, ve_freeze=0):
-    """Builds a red_config; `psf` is a 2-D float array (kept referenced by the config)."""
+                storage="f32", baseline="fp", sd_mu=0.0, ve_freeze=0, ve_stop_tol=0.0):
+    """Builds a red_config; `psf` is a 2-D float array (kept referenced by the config).
+    ve_stop_tol > 0 ends extrapolation at the first FP step whose relative change is below
+    it; plain baseline steps follow."""
     import numpy as np
     c = Config()
     lib().red_config_default(ctypes.byref(c))
@@ -191,6 +194,7 @@ def make_config(task="deblur", height=64, width=64, scale=1, psf=None, sigma=2 *
     c.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
     c.baseline = BASELINE_NAMES[baseline] if isinstance(baseline, str) else int(baseline)
     c.sd_mu, c.ve_freeze = float(sd_mu), int(ve_freeze)
+    c.ve_stop_tol = float(ve_stop_tol)
     c._psf_keepalive = psf
     return c
 

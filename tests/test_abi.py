@@ -77,6 +77,10 @@ def test_footprint_is_host_side_and_grows_with_size(lib):
     (dict(ve_freeze=-1), red.RED_EINVAL),
     (dict(ve="none", ve_freeze=1), red.RED_EINVAL),        # nothing to freeze
     (dict(ve_k=1, ve_m=0, ve_freeze=1), red.RED_EINVAL),   # a frozen cycle of 0 steps
+    (dict(ve_stop_tol=-1e-3), red.RED_EINVAL),
+    (dict(ve_stop_tol=float("nan")), red.RED_EINVAL),
+    (dict(ve="none", ve_stop_tol=1e-3), red.RED_EINVAL),   # no extrapolation to end
+    (dict(ve_freeze=2, ve_stop_tol=1e-3), red.RED_EINVAL), # frozen cycles keep no last iterate
 ])
 def test_invalid_configs_rejected_before_any_gpu_work(lib, kw, status):
     base = dict(height=64, width=64, psf=synth.uniform_psf(9))
@@ -101,7 +105,8 @@ def test_16_bit_storage_footprints(lib):
 
 @pytest.mark.parametrize("kw", [dict(baseline="sd"), dict(baseline="sd", sd_mu=1.5),
                                 dict(ve_freeze=2), dict(baseline="sd", ve="mpe", ve_k=9),
-                                dict(storage="f16", ve_freeze=1, ve_k=2)])
+                                dict(storage="f16", ve_freeze=1, ve_k=2),
+                                dict(ve_stop_tol=1e-3), dict(baseline="sd", ve="mpe", ve_stop_tol=2e-3)])
 def test_sd_and_frozen_configs_accepted(lib, kw):
     cfg = red.make_config(height=64, width=64, psf=synth.uniform_psf(9), **kw)
     out = ctypes.c_size_t()
