@@ -556,7 +556,9 @@ def _serving_input(seed):
             "y": np.ascontiguousarray(p.y.astype(np.float32))}
 
 
-SERVE_VARIANTS = (("rre", "rre", 0.0), ("plain_fp", "none", 0.0))
+# RRE with full cycling, plain FP, and RRE ended at a relative change of 3e-3 (30 x the
+# serving tolerance) with plain FP steps after it (red_config::ve_stop_tol)
+SERVE_VARIANTS = (("rre", "rre", 0.0), ("plain_fp", "none", 0.0), ("rre_then_fp", "rre", 3e-3))
 
 
 def serving_leg(red, n_req, rate_hz=SERVE_RATE_HZ, budget_gb=32, slots=32,
