@@ -76,6 +76,14 @@ class ClockSampler:
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation, the first query) runs before the timed
+        # region, not inside its first steps: wait for the first sample line (at most 5 s)
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -870,6 +878,8 @@ def main():
                    "fp_calls_per_solve": CALLS, "ve": "rre", "k": VE_K,
                    "l2": "flushed between timed steps (512 MB write)"},
         "solves_per_s": solves_per_s,
+        "step_ms_min_median_max": [float(np.min(step_ms)), float(np.median(step_ms)),
+                                   float(np.max(step_ms))],
         "launch_shapes": B.describe(),
         "roofline": {"bound": "alu", "kernel": "k_nlm", "achieved": nlm_achieved,
                      "peak": nlm_peak, "unit": "Top/s (FP32 lane-ops)",

@@ -141,3 +141,31 @@ def test_m_kappa_sweep_grid_and_best_pair(monkeypatch):
     assert (out["best_pair"]["rre"]["m"], out["best_pair"]["rre"]["kappa"]) == (10, 10)
     # the slowest pair (RRE, m = 0, kappa = 3: speed 1.15) still reaches it, at 175 calls
     assert out["grid"]["rre_m0_kappa3"]["calls_to_fp200_cost"] == [175, 175]
+
+
+def test_clock_sampler_starts_sampling_before_the_timed_region(tmp_path, monkeypatch):
+    """The sampler returns from start() only once nvidia-smi has written its first sample
+    (its start-up stays out of the timed steps), and stop() reads the median clock and the
+    active throttle reasons from the samples. A fake nvidia-smi on PATH stands in for the
+    real one: it starts after 0.3 s, then writes one line every 50 ms."""
+    import stat
+    import time
+    fake = tmp_path / "bin" / "nvidia-smi"
+    fake.parent.mkdir()
+    fake.write_text("#!/bin/sh\nsleep 0.3\n"
+                    "while true; do\n"
+                    "  echo '0, 1965, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.05\n"
+                    "done\n")
+    fake.chmod(fake.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", str(fake.parent) + os.pathsep + os.environ.get("PATH", ""))
+    monkeypatch.setenv("RED_CLOCKS_DIR", str(tmp_path / "clocks"))
+    s = bench.ClockSampler(0)
+    t0 = time.time()
+    s.start()
+    assert time.time() - t0 >= 0.25
+    assert os.path.getsize(s.path) > 0
+    time.sleep(0.2)
+    c = s.stop()
+    assert c["sm_mhz"] == 1965.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] >= 2
