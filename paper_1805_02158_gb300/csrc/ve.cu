@@ -32,6 +32,12 @@
 // with it the solve) skips the problem (VeArgs::skip_frozen), its xi stays in ve_coef, and every
 // cycle's combine applies it to x_m .. x_{m+kappa} (the combine never reads x_{m+kappa+1}
 // unless the extrapolation broke down, which a frozen gamma cannot).
+//
+// Extrapolation ended by its own criterion (the additional-iterations remark of Sec.
+// III-C): with ProbState::ve_stop_tol > 0, the first FP step whose relative change is
+// below it sets `ve_off` (in the Fourier solve's or the SR kernel's statistics epilogue);
+// from then on the Gram skips the problem and the combine passes the last FP iterate on
+// unchanged, as after a breakdown, so every later step is a plain baseline step.
 #include <algorithm>
 #include <mutex>
 #include <string>
