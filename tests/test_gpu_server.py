@@ -68,6 +68,38 @@ def test_server_alone_equals_mix():
     assert np.array_equal(alone0[0], mix[0])
 
 
+def test_server_ve_stop_tol_per_request():
+    """Requests that end extrapolation by their own criterion (red_config::ve_stop_tol, the
+    additional-iterations remark of Sec. III-C) share the server with requests of the same
+    problem that do not, and with other problems: each matches the single-problem solve
+    with its own setting, extrapolation count included, and the one that ended early made
+    fewer extrapolations (three, ending at FP step 16 or 17 of 40)."""
+    torch = torch_cuda()
+    p = synth.deblur_small(7)
+    jobs = [(p, 2.6e-3), (p, 0.0)] + [(q, 0.0) for q in requests()[1:3]]
+    S = red.Server(4 * GIB, 8)
+    outs, tickets = [], []
+    for q, t in jobs:
+        out = np.zeros((q.height, q.width), np.float32)
+        cfg = red.config_for(q, ve="rre", ve_k=5, ve_stop_tol=t)
+        tickets.append(S.submit(cfg, np.ascontiguousarray(q.y32), out, 40, 0.0))
+        outs.append(out)
+    stats = []
+    for tk in tickets:
+        st, s = S.wait(tk, 120000)
+        assert st == red.RED_OK, red.status_string(st)
+        stats.append(s)
+    S.close()
+    for (q, t), out, s in zip(jobs, outs, stats):
+        P = red.Problem(red.config_for(q, ve="rre", ve_k=5, ve_stop_tol=t), to_dev(q.y))
+        ref = torch.empty((q.height, q.width), device="cuda")
+        d = P.solve(to_dev(q.x0), ref, 40)
+        assert s["fp_calls"] == d["fp_calls"] == 40
+        assert s["ve_steps"] == d["ve_steps"]
+        assert rel_l2(out, to_host(ref)) <= 1e-4
+    assert stats[0]["ve_steps"] == 3 < stats[1]["ve_steps"]
+
+
 def test_server_groups_of_different_sizes_run_concurrently():
     """Requests of both tasks in several size classes (separate groups, streams and
     shared-memory footprints) all complete, and one of them equals its solve alone."""
