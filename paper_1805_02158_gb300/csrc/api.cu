@@ -190,6 +190,18 @@ int sr_cluster_override() {
   return (v == 8 || v == 10 || v == 12 || v == 16) ? v : -1;
 }
 
+// RED_NLM_SHAPE=<w>,<o> forces the NLM launch shape: w warp tiles per CTA (1, 2 or 4) at
+// the register budget of o resident CTAs per SM (3 or 4). Other values are ignored.
+void nlm_shape_override(int *wy, int *occ) {
+  const char *e = std::getenv("RED_NLM_SHAPE");
+  int w = 0, o = 0;
+  if (!e || std::sscanf(e, "%d,%d", &w, &o) != 2) return;
+  if ((w == 1 || w == 2 || w == 4) && (o == 3 || o == 4)) {
+    *wy = w;
+    *occ = o;
+  }
+}
+
 void Plan::build(const std::vector<ProbDev> &pds, const LaunchCfg &cfg, cudaStream_t stream,
                  bool async) {
   if (!async) release();
@@ -578,6 +590,7 @@ red_status red_create_problem(const red_config *cfg, const void *y_dev, void *st
     fill_prob_dev(P.get());
     if (fft_cluster_override() >= 0) P->lc.fft_cluster = fft_cluster_override();
     if (sr_cluster_override() > 0) P->lc.sr_cluster = sr_cluster_override();
+    nlm_shape_override(&P->lc.nlm_wy, &P->lc.nlm_occ);
     problem_upload_pd(P.get());
     char *b = static_cast<char *>(P->block);
     CUDA_OK(cudaMemcpyAsync(b + P->L.psf, P->psf.data(), sizeof(float) * P->psf.size(),

@@ -328,6 +328,7 @@ void ensure_ready(red_batch_s *b, cudaStream_t s) {
     }
     if (fft_cluster_override() >= 0) c.fft_cluster = fft_cluster_override();
     if (sr_cluster_override() > 0) c.sr_cluster = sr_cluster_override();
+    nlm_shape_override(&c.nlm_wy, &c.nlm_occ);
     b->lc = c;
     b->plan.build(b->pds, c);
     upload_pds(b);

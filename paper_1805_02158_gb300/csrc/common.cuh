@@ -129,7 +129,7 @@ struct VeArgs {
 
 // ---- host-side launch helpers (defined in the .cu files) -------------------------------
 struct LaunchCfg {
-  int nlm_wy = 4;          // warps per NLM CTA (tile height = 8 * nlm_wy rows)
+  int nlm_wy = 4;          // warps per NLM CTA (one 60 x kNlmR warp tile each)
   int nlm_occ = 4;         // resident NLM CTAs per SM the register budget allows (3 or 4)
   int fft_rows = 0;        // rows per row-FFT CTA (0 = auto from the row length)
   int fft_cols = 0;        // columns per column-FFT CTA (0 = auto from the column length)

@@ -98,6 +98,7 @@ std::vector<CycleOp> cycle_ops(int ve, int k, int m, int freeze);
 void prepare_launch_attrs(const Plan &pl);
 int fft_cluster_override();   // RED_FFT_CLUSTER, or -1 when unset
 int sr_cluster_override();    // RED_SR_CLUSTER (8, 10, 12 or 16), or -1 when unset
+void nlm_shape_override(int *wy, int *occ);   // RED_NLM_SHAPE=<w>,<o>; unchanged when unset
 
 }  // namespace red
 

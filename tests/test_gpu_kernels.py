@@ -86,6 +86,36 @@ def test_nlm_constant_and_shift_properties():
     assert float((f2 - f1 - 16.0).abs().max()) <= 2e-3
 
 
+def test_nlm_result_does_not_depend_on_the_launch_shape(monkeypatch):
+    """Every NLM launch shape the autotuner chooses between (1, 2 or 4 warp tiles per CTA,
+    register budget for 3 or 4 CTAs per SM; forced with RED_NLM_SHAPE) gives the same
+    denoiser output and the same 12-step RRE solves bit for bit, for a single problem and
+    for a batch of two sizes: the pixel-to-lane grid is fixed in image coordinates."""
+    torch = torch_cuda()
+    probs = [deblur_problem(64, 64, 3), deblur_problem(72, 96, 5, synth.gaussian_psf(7, 1.4))]
+    ref = None
+    for wy in (1, 2, 4):
+        for occ in (3, 4):
+            monkeypatch.setenv("RED_NLM_SHAPE", f"{wy},{occ}")
+            Ps = [red.Problem(red.config_for(q, ve="rre", ve_k=5), to_dev(q.y)) for q in probs]
+            x0s = [to_dev(f32(q.x0)) for q in probs]
+            f = torch.empty_like(x0s[1])
+            Ps[1].denoise(x0s[1], f)
+            single = torch.empty_like(x0s[0])
+            Ps[0].solve(x0s[0], single, 12)
+            B = red.Batch(Ps)
+            outs = [torch.empty_like(x) for x in x0s]
+            B.solve(x0s, outs, 12, 0.0)
+            shape = B.describe()
+            assert (shape["nlm_warps_per_cta"], shape["nlm_ctas_per_sm"]) == (wy, occ)
+            got = [to_host(f), to_host(single)] + [to_host(o) for o in outs]
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(got, ref):
+                    np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("shape,psf", [((64, 64), synth.uniform_psf(9)),
                                        ((48, 72), synth.gaussian_psf(7, 1.6)),
                                        ((96, 128), synth.gaussian_psf(25, 1.6)),
